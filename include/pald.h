@@ -1,0 +1,165 @@
+/*
+ * pald.h - C ABI of libpald: the two O(n^3) triplet passes of partitioned
+ * local depths (PaLD) on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method: Devarakonda & Ballard, "Sequential and Shared-Memory Parallel
+ * Algorithms for Partitioned Local Depths".  For an n x n distance matrix D:
+ *
+ *   pass 1  local focus sizes (Sec. 2 definition of the local focus):
+ *           u_xy = #{ z : d_xz <= d_xy  or  d_yz <= d_xy },  every x, y;
+ *   pass 2  cohesion (Sec. 2, eq. (cohesion) written out as eq. (fxz), with
+ *           the half-credit tie split of Sec. 5):
+ *           c_xz = 1/(n-1) * sum_{y != x} [z in U_xy] * w(d_zx, d_zy) / u_xy,
+ *           w(p, q) = 1 if p < q, 1/2 if p == q, 0 if p > q.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are dense, row-major, n x n, element (i, j) at index i*n + j,
+ *     and live in device memory that the CALLER allocated and owns (unless an
+ *     entry point says "host").  The library never frees caller memory.
+ *   - Input contract for D (checked only when pald_opts.validate != 0 or by
+ *     pald_validate): exactly symmetric bit for bit, +0.0 on the diagonal,
+ *     every entry finite and >= +0.0 (no NaN, no negative value, no -0.0),
+ *     every positive entry >= 2^-100, and (largest entry) / (smallest positive
+ *     entry) < 2^100.  PaLD only compares distances, so a matrix outside the
+ *     last two limits can be rescaled by a power of two without changing u or
+ *     C.  Results for inputs that break the contract are unspecified.
+ *   - Calls are asynchronous and ordered on `stream` (NULL = the legacy
+ *     default stream), except that validation copies one small status word to
+ *     the host and synchronises `stream`.
+ *   - Scratch memory that a call needs is taken with cudaMallocAsync on
+ *     `stream` and released on the same stream before the call returns.
+ *   - Every function returns a status and never aborts, traps or prints.
+ *     On any error the contents of the outputs are unspecified.
+ */
+#ifndef PALD_H
+#define PALD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t, so callers can pass a CUDA stream directly. */
+typedef struct CUstream_st* pald_stream_t;
+
+typedef enum pald_status {
+  PALD_OK = 0,
+  PALD_ERR_INVALID_ARG = 1,    /* null pointer, n < 2, bad count/offset, bad opts */
+  PALD_ERR_NOT_SYMMETRIC = 2,  /* validation: d_ij and d_ji differ in some bit */
+  PALD_ERR_BAD_DIAGONAL = 3,   /* validation: a diagonal entry is not +0.0 */
+  PALD_ERR_BAD_VALUE = 4,      /* validation: NaN, inf, negative, -0.0, or out of range */
+  PALD_ERR_CUDA = 5,           /* a CUDA runtime call failed (see pald_last_cuda_error) */
+  PALD_ERR_NO_MEMORY = 6,      /* scratch allocation failed */
+  PALD_ERR_TIMEOUT = 7,        /* reserved: a bounded device-side wait gave up */
+  PALD_ERR_UNSUPPORTED = 8     /* size beyond what this build handles */
+} pald_status;
+
+/* Accumulation of the cohesion sums (pass 2). */
+enum {
+  /* FP32 partial sums over 16 consecutive y, folded into an FP32 running sum
+   * with an error-free TwoSum whose error is carried into the next partial;
+   * FP64 final merge, 1/(n-1) in FP64, one rounding to FP32 (default). */
+  PALD_ACCUM_COMPENSATED = 0,
+  /* one FP32 running sum per entry, normalised in FP32 (precision baseline) */
+  PALD_ACCUM_PLAIN = 1
+};
+
+typedef struct pald_opts {
+  int32_t validate;     /* nonzero: check the input contract before computing */
+  int32_t accum_mode;   /* PALD_ACCUM_COMPENSATED or PALD_ACCUM_PLAIN */
+  int32_t schedule_id;  /* -1 = automatic tile schedule; >= 0 forces one (pald_schedule_name) */
+  int32_t reserved;     /* must be 0 */
+} pald_opts;          /* a NULL opts pointer means {0, PALD_ACCUM_COMPENSATED, -1, 0} */
+
+/*
+ * pald_focus - pass 1, local focus sizes (Sec. 2, the definition of U_xy;
+ * computed pair by pair like the pairwise algorithm of Sec. 3.1, blocked over
+ * x, y and z like Sec. 3.2).
+ *   D  device, n x n FP32, the input contract above.
+ *   n  order of the matrix, 2 <= n <= 2^20 (n*n elements addressable).
+ *   U  device, n x n int32, written completely: U[x*n+y] = u_xy, including the
+ *      diagonal u_xx = #{z : d_xz <= 0}.  U is symmetric.
+ * Errors: INVALID_ARG (null pointer, n out of range, bad opts); validation
+ * errors; CUDA; NO_MEMORY.
+ */
+pald_status pald_focus(const float* D, int64_t n, int32_t* U,
+                       const pald_opts* opts, pald_stream_t stream);
+
+/*
+ * pald_cohesion - pass 2, the cohesion matrix (Sec. 2 eq. (cohesion) in the
+ * form of eq. (fxz), ties split per Sec. 5, normalised by 1/(n-1)).
+ *   D  device, n x n FP32 (the same matrix pald_focus saw).
+ *   U  device, n x n int32 focus sizes as written by pald_focus (a saved U
+ *      can be passed back to resume after pass 1); only u_xy for x != y is
+ *      read.  Each such entry must be in [2, n].
+ *   C  device, n x n FP32, written completely: C[x*n+z] = c_xz.
+ * Errors: as pald_focus.
+ */
+pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
+                          const pald_opts* opts, pald_stream_t stream);
+
+/*
+ * pald_batched - both passes for `count` independent matrices of uneven order
+ * in one persistent launch per pass, replayed from a cached CUDA graph.
+ *   count     number of matrices, 1 <= count <= 2^20.
+ *   n_host    host array [count], orders n_i with 2 <= n_i <= 4096.
+ *   off_host  host array [count], element offset of matrix i in D, U and C;
+ *             each a multiple of 4 (16-byte aligned); the regions
+ *             [off_i, off_i + n_i^2) must not overlap.
+ *   D         device FP32, matrix i is n_i x n_i row-major at D + off_i.
+ *   U         device int32, same layout as D; receives u for every matrix.
+ *   C         device FP32, same layout as D; receives C for every matrix.
+ * The first call for a given (count, n, off, D, U, C, opts) builds a work
+ * plan and a CUDA graph (host work, and it synchronises `stream`); later calls
+ * with the same arguments only launch the graph.  pald_release() frees them.
+ * Errors: INVALID_ARG (bad count, n_i, misaligned or overlapping offsets);
+ * validation errors; CUDA; NO_MEMORY.
+ */
+pald_status pald_batched(int32_t count, const int64_t* n_host, const int64_t* off_host,
+                         const float* D, int32_t* U, float* C,
+                         const pald_opts* opts, pald_stream_t stream);
+
+/*
+ * pald_host - convenience call on HOST buffers: copies D to the device, runs
+ * both passes, copies U and C back, and synchronises.  Device buffers are
+ * allocated and freed inside the call.  Pinned host memory makes the copies
+ * faster but is not required.
+ *   D_host  host n x n FP32; U_host host n x n int32; C_host host n x n FP32.
+ * Errors: as pald_focus and pald_cohesion.
+ */
+pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_host,
+                      const pald_opts* opts);
+
+/*
+ * pald_validate - check the input contract of D (see above) on the device.
+ * Reads D twice (row-wise and transposed), copies one status word to the
+ * host and synchronises `stream`.  Returns PALD_OK or the first violation
+ * found in the order NOT_SYMMETRIC, BAD_DIAGONAL, BAD_VALUE.
+ */
+pald_status pald_validate(const float* D, int64_t n, pald_stream_t stream);
+
+/* Number of built-in tile schedules and the name of schedule `id` (static
+ * string, or NULL if id is out of range).  Used by the autotuner. */
+int32_t pald_schedule_count(void);
+const char* pald_schedule_name(int32_t id);
+
+/* Static, human-readable description of a status code. */
+const char* pald_status_string(pald_status status);
+
+/* The cudaError_t value behind the most recent PALD_ERR_CUDA on this thread. */
+int32_t pald_last_cuda_error(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t pald_version(void);
+
+/* Frees the cached batched plans and graphs of every device.  Must not be
+ * called while a batched graph is still running. */
+void pald_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PALD_H */

@@ -1,0 +1,39 @@
+"""GB300-native PaLD: the two triplet passes of partitioned local depths.
+
+The compute lives in ``libpald.so`` (hand-written sm_103a CUDA kernels behind
+the C ABI of ``include/pald.h``).  This package is a thin binding over that
+ABI: it checks tensors, passes raw device pointers and the current CUDA
+stream, and turns status codes into exceptions.  There is no CPU fallback:
+every call fails loudly if the library is not built or no GPU is present.
+
+    from paper_2307_16652_gb300 import pald_focus, pald_cohesion
+    pald_focus(D, U)          # D: (n, n) float32 CUDA tensor, U: (n, n) int32
+    pald_cohesion(D, U, C)    # C: (n, n) float32
+
+The seeded workload generators are in :mod:`paper_2307_16652_gb300.inputs`.
+"""
+from __future__ import annotations
+
+from .binding import (  # noqa: F401
+    PALD_ACCUM_COMPENSATED,
+    PALD_ACCUM_PLAIN,
+    PaldError,
+    lib,
+    library_path,
+    pald_batched,
+    pald_cohesion,
+    pald_focus,
+    pald_host,
+    pald_release,
+    pald_schedule_count,
+    pald_schedule_name,
+    pald_status_string,
+    pald_validate,
+    pald_version,
+)
+
+__all__ = [
+    "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PaldError", "lib", "library_path",
+    "pald_batched", "pald_cohesion", "pald_focus", "pald_host", "pald_release",
+    "pald_schedule_count", "pald_schedule_name", "pald_status_string", "pald_validate", "pald_version",
+]

@@ -1,0 +1,210 @@
+"""ctypes binding of libpald (argument marshalling only).
+
+Each function has the name of the C entry point it calls.  Device tensors
+are passed as raw pointers together with the current torch CUDA stream, so
+the kernels are ordered with the caller's other work.  Loading the library
+does not build it: run ``python -m paper_2307_16652_gb300.build`` (or
+``__graft_entry__.build()``) first.  A missing library raises; there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PALD_ACCUM_COMPENSATED = 0
+PALD_ACCUM_PLAIN = 1
+
+_STATUS = {
+    0: "PALD_OK", 1: "PALD_ERR_INVALID_ARG", 2: "PALD_ERR_NOT_SYMMETRIC", 3: "PALD_ERR_BAD_DIAGONAL",
+    4: "PALD_ERR_BAD_VALUE", 5: "PALD_ERR_CUDA", 6: "PALD_ERR_NO_MEMORY", 7: "PALD_ERR_TIMEOUT",
+    8: "PALD_ERR_UNSUPPORTED",
+}
+
+
+class PaldError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        name = _STATUS.get(status, str(status))
+        msg = f"{where}: {name} ({_lib().pald_status_string(status).decode()})"
+        if status == 5:
+            msg += f", cudaError={_lib().pald_last_cuda_error()}"
+        super().__init__(msg)
+
+
+class PaldOpts(ctypes.Structure):
+    _fields_ = [("validate", ctypes.c_int32), ("accum_mode", ctypes.c_int32),
+                ("schedule_id", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lock = threading.Lock()
+_handle: ctypes.CDLL | None = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib() -> ctypes.CDLL:
+    global _handle
+    with _lock:
+        if _handle is not None:
+            return _handle
+        path = library_path()
+        if not os.path.exists(path):
+            raise ImportError(f"libpald is not built ({path} missing); run paper_2307_16652_gb300.build.build()")
+        h = ctypes.CDLL(path)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+        op = ctypes.POINTER(PaldOpts)
+        h.pald_focus.argtypes = [vp, i64, vp, op, vp]
+        h.pald_cohesion.argtypes = [vp, vp, i64, vp, op, vp]
+        h.pald_batched.argtypes = [i32, vp, vp, vp, vp, vp, op, vp]
+        h.pald_host.argtypes = [vp, i64, vp, vp, op]
+        h.pald_validate.argtypes = [vp, i64, vp]
+        for f in (h.pald_focus, h.pald_cohesion, h.pald_batched, h.pald_host, h.pald_validate):
+            f.restype = ctypes.c_int
+        h.pald_status_string.argtypes = [ctypes.c_int]
+        h.pald_status_string.restype = ctypes.c_char_p
+        h.pald_schedule_name.argtypes = [i32]
+        h.pald_schedule_name.restype = ctypes.c_char_p
+        h.pald_schedule_count.restype = i32
+        h.pald_last_cuda_error.restype = i32
+        h.pald_version.restype = i32
+        h.pald_release.restype = None
+        _handle = h
+        return h
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded libpald handle (raises if it is not built)."""
+    return _lib()
+
+
+def _opts(validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1):
+    return PaldOpts(int(bool(validate)), int(accum_mode), int(schedule_id), 0)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(t, dtype, n=None, name="tensor"):
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (there is no CPU path)")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if n is not None and tuple(t.shape) != (n, n):
+        raise ValueError(f"{name} must have shape ({n}, {n}), got {tuple(t.shape)}")
+    return t.data_ptr()
+
+
+def _raise(st, where):
+    if st != 0:
+        raise PaldError(st, where)
+
+
+def pald_focus(D, U, *, validate=False, schedule_id=-1, stream=None):
+    """Pass 1: U[x, y] = u_xy (int32) from the FP32 distance matrix D."""
+    import torch
+
+    n = D.shape[0]
+    o = _opts(validate, PALD_ACCUM_COMPENSATED, schedule_id)
+    st = _lib().pald_focus(_check(D, torch.float32, n, "D"), n, _check(U, torch.int32, n, "U"),
+                           ctypes.byref(o), _stream_ptr(stream))
+    _raise(st, "pald_focus")
+    return U
+
+
+def pald_cohesion(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1, stream=None):
+    """Pass 2: C[x, z] = c_xz (FP32) from D and the focus sizes U."""
+    import torch
+
+    n = D.shape[0]
+    o = _opts(validate, accum_mode, schedule_id)
+    st = _lib().pald_cohesion(_check(D, torch.float32, n, "D"), _check(U, torch.int32, n, "U"), n,
+                              _check(C, torch.float32, n, "C"), ctypes.byref(o), _stream_ptr(stream))
+    _raise(st, "pald_cohesion")
+    return C
+
+
+def pald_batched(ns, offs, D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, stream=None):
+    """Both passes for packed matrices: matrix i is ns[i] x ns[i] at element offs[i]."""
+    import numpy as np
+    import torch
+
+    ns = np.ascontiguousarray(np.asarray(ns, dtype=np.int64))
+    offs = np.ascontiguousarray(np.asarray(offs, dtype=np.int64))
+    if ns.shape != offs.shape or ns.ndim != 1:
+        raise ValueError("ns and offs must be 1-D arrays of equal length")
+    for t, dt, nm in ((D, torch.float32, "D"), (U, torch.int32, "U"), (C, torch.float32, "C")):
+        _check(t, dt, None, nm)
+    need = int((offs + ns * ns).max())
+    if min(D.numel(), U.numel(), C.numel()) < need:
+        raise ValueError("packed buffers are smaller than the last matrix")
+    o = _opts(validate, accum_mode, -1)
+    st = _lib().pald_batched(len(ns), ns.ctypes.data, offs.ctypes.data, D.data_ptr(), U.data_ptr(),
+                             C.data_ptr(), ctypes.byref(o), _stream_ptr(stream))
+    _raise(st, "pald_batched")
+
+
+def pald_host(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED):
+    """Both passes on host (numpy or CPU torch) buffers; copies in and out."""
+    import numpy as np
+
+    def ptr(a, dtype):
+        if hasattr(a, "data_ptr"):
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError("host buffers must be contiguous CPU tensors")
+            return a.data_ptr()
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffers must be C-contiguous of the right dtype")
+        return a.ctypes.data
+
+    n = D.shape[0]
+    o = _opts(validate, accum_mode, -1)
+    st = _lib().pald_host(ptr(D, np.float32), n, ptr(U, np.int32), ptr(C, np.float32), ctypes.byref(o))
+    _raise(st, "pald_host")
+
+
+def pald_validate(D, *, stream=None):
+    """Check the input contract of D; returns the status code (0 = valid)."""
+    import torch
+
+    n = D.shape[0]
+    return _lib().pald_validate(_check(D, torch.float32, n, "D"), n, _stream_ptr(stream))
+
+
+def pald_schedule_count() -> int:
+    return _lib().pald_schedule_count()
+
+
+def pald_schedule_name(i: int):
+    s = _lib().pald_schedule_name(i)
+    return s.decode() if s is not None else None
+
+
+def pald_status_string(status: int) -> str:
+    return _lib().pald_status_string(status).decode()
+
+
+def pald_version() -> int:
+    return _lib().pald_version()
+
+
+def pald_release() -> None:
+    _lib().pald_release()

@@ -1,0 +1,184 @@
+// extern "C" entry points of libpald (declared in include/pald.h).
+//
+// This file holds argument checking, scratch management, validation and
+// dispatch; the arithmetic of both passes lives in the kernels.
+#include <cmath>
+#include <cstring>
+
+#include "pald_internal.cuh"
+
+namespace pald {
+
+thread_local int32_t g_last_cuda_error = 0;
+
+pald_status cuda_fail(cudaError_t e) {
+  g_last_cuda_error = static_cast<int32_t>(e);
+  return e == cudaErrorMemoryAllocation ? PALD_ERR_NO_MEMORY : PALD_ERR_CUDA;
+}
+
+bool opts_ok(const pald_opts* o) {
+  if (!o) return true;
+  if (o->reserved != 0) return false;
+  if (o->accum_mode != PALD_ACCUM_COMPENSATED && o->accum_mode != PALD_ACCUM_PLAIN) return false;
+  if (o->schedule_id < -1 || o->schedule_id > 1) return false;
+  return true;
+}
+
+pald_opts opts_or_default(const pald_opts* o) {
+  pald_opts d{0, PALD_ACCUM_COMPENSATED, -1, 0};
+  return o ? *o : d;
+}
+
+constexpr int64_t kMaxN = int64_t(1) << 20;
+
+// Maps a scan result (already on the host) to a status.
+pald_status status_from_scan(const ScanResult& r) {
+  if (r.flags & kFlagAsymmetric) return PALD_ERR_NOT_SYMMETRIC;
+  if (r.flags & kFlagBadDiagonal) return PALD_ERR_BAD_DIAGONAL;
+  if (r.flags & (kFlagBadValue | kFlagRange)) return PALD_ERR_BAD_VALUE;
+  if (r.inv_min_pos_bits != 0u) {
+    uint32_t mn = ~r.inv_min_pos_bits, mx = r.max_bits;
+    float fmn, fmx;
+    std::memcpy(&fmn, &mn, 4);
+    std::memcpy(&fmx, &mx, 4);
+    if (static_cast<double>(fmx) >= std::ldexp(static_cast<double>(fmn), 100)) return PALD_ERR_BAD_VALUE;
+  }
+  return PALD_OK;
+}
+
+// Runs the scan (and validation when asked) into `scratch`; when validating,
+// copies the result back and synchronises the stream.
+pald_status scan_and_check(const float* D, int64_t n, ScanResult* scratch, bool validate, cudaStream_t s) {
+  cudaError_t e = launch_scan(D, n, scratch, validate, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!validate) return PALD_OK;
+  ScanResult host{};
+  e = cudaMemcpyAsync(&host, scratch, sizeof host, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return status_from_scan(host);
+}
+
+// Stream-ordered scratch that is released on every exit path.
+struct Scratch {
+  void* p = nullptr;
+  cudaStream_t s;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  cudaError_t alloc(size_t bytes) { return cudaMallocAsync(&p, bytes, s); }
+  ~Scratch() {
+    if (p) cudaFreeAsync(p, s);
+  }
+};
+
+}  // namespace pald
+
+using namespace pald;
+
+extern "C" {
+
+pald_status pald_focus(const float* D, int64_t n, int32_t* U, const pald_opts* opts, pald_stream_t stream) {
+  if (!D || !U || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
+  const pald_opts o = opts_or_default(opts);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Scratch scratch(s);
+  cudaError_t e = scratch.alloc(sizeof(ScanResult));
+  if (e != cudaSuccess) return cuda_fail(e);
+  auto* scan = static_cast<ScanResult*>(scratch.p);
+  pald_status st = scan_and_check(D, n, scan, o.validate != 0, s);
+  if (st != PALD_OK) return st;
+  e = launch_focus(D, n, U, scan, o.schedule_id, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return PALD_OK;
+}
+
+pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C, const pald_opts* opts,
+                          pald_stream_t stream) {
+  if (!D || !U || !C || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
+  const pald_opts o = opts_or_default(opts);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (o.validate) {
+    Scratch scratch(s);
+    cudaError_t e = scratch.alloc(sizeof(ScanResult));
+    if (e != cudaSuccess) return cuda_fail(e);
+    pald_status st = scan_and_check(D, n, static_cast<ScanResult*>(scratch.p), true, s);
+    if (st != PALD_OK) return st;
+  }
+  cudaError_t e = launch_cohesion(D, U, n, C, o.accum_mode, o.schedule_id, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return PALD_OK;
+}
+
+pald_status pald_validate(const float* D, int64_t n, pald_stream_t stream) {
+  if (!D || n < 2 || n > kMaxN) return PALD_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  Scratch scratch(s);
+  cudaError_t e = scratch.alloc(sizeof(ScanResult));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return scan_and_check(D, n, static_cast<ScanResult*>(scratch.p), true, s);
+}
+
+pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_host, const pald_opts* opts) {
+  if (!D_host || !U_host || !C_host || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
+  const size_t bytes = static_cast<size_t>(n) * static_cast<size_t>(n) * 4u;
+  cudaStream_t s = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e);
+  float* dD = nullptr;
+  int32_t* dU = nullptr;
+  float* dC = nullptr;
+  pald_status st = PALD_OK;
+  do {
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&dD), bytes, s)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&dU), bytes, s)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync(reinterpret_cast<void**>(&dC), bytes, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(dD, D_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    st = pald_focus(dD, n, dU, opts, reinterpret_cast<pald_stream_t>(s));
+    if (st != PALD_OK) break;
+    pald_opts o2 = opts_or_default(opts);
+    o2.validate = 0;  // already checked by pass 1 when asked
+    st = pald_cohesion(dD, dU, n, dC, &o2, reinterpret_cast<pald_stream_t>(s));
+    if (st != PALD_OK) break;
+    if ((e = cudaMemcpyAsync(U_host, dU, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(C_host, dC, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+  } while (false);
+  if (dD) cudaFreeAsync(dD, s);
+  if (dU) cudaFreeAsync(dU, s);
+  if (dC) cudaFreeAsync(dC, s);
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaStreamDestroy(s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (st != PALD_OK) return st;
+  if (e2 != cudaSuccess) return cuda_fail(e2);
+  return PALD_OK;
+}
+
+int32_t pald_schedule_count(void) { return 2; }
+
+const char* pald_schedule_name(int32_t id) {
+  switch (id) {
+    case 0: return "focus 128x128 tiles (8x8 per thread) / cohesion 64x64 tiles (4x4 per thread)";
+    case 1: return "focus 64x64 tiles (4x4 per thread) / cohesion 32x32 tiles (4x4 per thread)";
+    default: return nullptr;
+  }
+}
+
+const char* pald_status_string(pald_status status) {
+  switch (status) {
+    case PALD_OK: return "ok";
+    case PALD_ERR_INVALID_ARG: return "invalid argument";
+    case PALD_ERR_NOT_SYMMETRIC: return "distance matrix is not exactly symmetric";
+    case PALD_ERR_BAD_DIAGONAL: return "distance matrix diagonal is not +0.0";
+    case PALD_ERR_BAD_VALUE: return "distance matrix has a NaN, infinite, negative, -0.0 or out-of-range entry";
+    case PALD_ERR_CUDA: return "CUDA runtime error";
+    case PALD_ERR_NO_MEMORY: return "out of device memory";
+    case PALD_ERR_TIMEOUT: return "device-side wait timed out";
+    case PALD_ERR_UNSUPPORTED: return "unsupported size";
+  }
+  return "unknown status";
+}
+
+int32_t pald_last_cuda_error(void) { return g_last_cuda_error; }
+
+int32_t pald_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+"""Full-size workloads on the GPU: the n = 65536 matrix (sampled rows against
+the oracle, global invariants on everything) and the batched workload (2000
+matrices, one graph replay, against the oracle and the single-matrix path)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_2307_16652_gb300 import binding, build, inputs
+
+pytestmark = pytest.mark.gpu
+C_RTOL = 2e-7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    binding.lib()
+
+
+def check_rows(U_rows, C_rows, Ur, Cr):
+    assert np.array_equal(U_rows, Ur)
+    Cr = np.asarray(Cr, np.float64)
+    C_rows = np.asarray(C_rows, np.float64)
+    nz = Cr != 0
+    assert np.all(C_rows[~nz] == 0)
+    rel = np.abs(C_rows[nz] - Cr[nz]) / Cr[nz]
+    assert rel.max() <= C_RTOL, f"max relative error {rel.max():.3e}"
+    return rel.max(), rel.mean()
+
+
+def test_paper_65536_sampled_rows_and_invariants():
+    n = 65536
+    D = inputs.euclidean_fp32_torch(inputs.paper_points(n), "cuda")
+    U = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    binding.pald_focus(D, U)
+    binding.pald_cohesion(D, U, C)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(65536)
+    rows = np.unique(np.concatenate([[0, n - 1], rng.choice(n, size=14, replace=False)]))
+    Dh = D.cpu().numpy()
+    Ur, Cr = oracle.rows(Dh, rows)
+    idx = torch.from_numpy(rows).cuda()
+    mx, mean = check_rows(U[idx].cpu().numpy(), C[idx].cpu().numpy(), Ur, Cr)
+    print(f"paper-65536 sampled {len(rows)} rows: max rel {mx:.3e} mean {mean:.3e}")
+    del Dh
+    # invariants on the whole output, block by block on the device
+    blk = 4096
+    total = torch.zeros((), dtype=torch.float64, device="cuda")
+    for r0 in range(0, n, blk):
+        Ub = U[r0:r0 + blk]
+        assert torch.equal(Ub, U[:, r0:r0 + blk].transpose(0, 1))
+        off = Ub.clone()
+        ar = torch.arange(min(blk, n - r0), device="cuda")
+        off[ar, ar + r0] = n  # ignore the diagonal below
+        assert int(off.min()) >= 2 and int(Ub.max()) <= n
+        Cb = C[r0:r0 + blk]
+        assert float(Cb.min()) >= 0.0
+        total += Cb.double().sum()
+    assert abs(float(total) - n / 2) < 1e-6 * n
+
+
+def _batched_inputs(count):
+    ns = inputs.batched_sizes(count)
+    offs, total = inputs.packed_offsets(ns)
+    Dh = np.zeros(total, np.float32)
+    mats = []
+    for i, n, Di in inputs.batched_matrices(count):
+        Dh[offs[i]:offs[i] + n * n] = Di.ravel()
+        mats.append(Di)
+    return ns, offs, total, Dh, mats
+
+
+def test_batched_against_oracle_and_single_path():
+    count = 2000
+    ns, offs, total, Dh, mats = _batched_inputs(count)
+    D = torch.from_numpy(Dh).cuda()
+    U = torch.zeros(total, dtype=torch.int32, device="cuda")
+    C = torch.zeros(total, dtype=torch.float32, device="cuda")
+    binding.pald_batched(ns, offs, D, U, C)
+    binding.pald_batched(ns, offs, D, U, C)  # second call replays the cached graph
+    torch.cuda.synchronize()
+    Uh, Chh = U.cpu().numpy(), C.cpu().numpy()
+    # every matrix against the single-matrix kernels: u and C bit for bit
+    for i in range(count):
+        n = int(ns[i])
+        Di = torch.from_numpy(mats[i]).cuda()
+        Ui = torch.empty((n, n), dtype=torch.int32, device="cuda")
+        Ci = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        binding.pald_focus(Di, Ui)
+        binding.pald_cohesion(Di, Ui, Ci)
+        ub = Uh[offs[i]:offs[i] + n * n].reshape(n, n)
+        cb = Chh[offs[i]:offs[i] + n * n].reshape(n, n)
+        assert np.array_equal(ub, Ui.cpu().numpy()), f"matrix {i}"
+        assert np.array_equal(cb, Ci.cpu().numpy()), f"matrix {i}"
+    # a spread of matrices (smallest, largest and every 25th) against the oracle
+    pick = sorted(set([int(np.argmin(ns)), int(np.argmax(ns))] + list(range(0, count, 25))))
+    worst = 0.0
+    for i in pick:
+        n = int(ns[i])
+        Ur, Cr = oracle.focus_and_cohesion(mats[i])
+        mx, _ = check_rows(Uh[offs[i]:offs[i] + n * n].reshape(n, n), Chh[offs[i]:offs[i] + n * n].reshape(n, n),
+                           Ur, Cr)
+        worst = max(worst, mx)
+    print(f"batched: {len(pick)} matrices vs oracle, max rel {worst:.3e}")
+    binding.pald_release()
