@@ -6,9 +6,10 @@
 //     to c_xz:  [d_xz <= min(d_xy, d_zy)] * w(d_xz, d_zy) * r_xy
 //     to c_zx:  [d_xz <= min(d_xy, d_zy)] * w(d_xz, d_xy) * r_zy
 // with r = 1/u and w(b, a) = 0, 1/2, 1 for a < b, a == b, a > b.  (z in U_xy
-// together with d_zx <= d_zy is the same as d_xz <= min(d_xy, d_zy).)  The
-// diagonal of R is set to 0, which removes the excluded y == x term exactly,
-// duplicate points included.
+// together with d_zx <= d_zy is the same as d_xz <= min(d_xy, d_zy).)  R has
+// a zero diagonal, which removes the excluded y == x term exactly, duplicate
+// points included.  R = 1/u is precomputed once per matrix (the reciprocal
+// loop between the passes, Sec. 6 figures), not in this kernel.
 //
 // Per (x, z, y) the inner loop issues six instructions, all of them exact
 // FP32 decisions on the input values:
@@ -25,11 +26,14 @@
 // to 0 or 1.  b = 0 uses s = 2^127, c = 1/2 (inputs have no positive entry
 // below 2^-100).
 //
-// Accumulation (PALD_ACCUM_COMPENSATED): S holds an FP32 partial over one
-// 16-y stage; after each stage it is folded into the running FP32 sum H with
-// an error-free TwoSum, and the exact rounding error becomes the start of the
-// next partial, so nothing is lost between stages.  At the end H + S is
-// formed in FP64, multiplied by 1/(n-1) in FP64 and rounded once to FP32.
+// Accumulation (PALD_ACCUM_COMPENSATED): the pair {S_xz, S_zx} is an FP32
+// partial over 4 consecutive y.  Every 4 y it is folded into the running sums
+// {H_xz, H_zx}, which start at the bias B = 4: a partial never exceeds
+// 4 * 1/2 plus the carried error, so |H| >= |S| always holds and Fast2Sum
+// (three adds, done as packed f32x2 ops on both accumulators at once) is
+// error-free.  Its exact error becomes the start of the next partial, so
+// nothing is lost between chunks.  At the end H - B + S is formed in FP64,
+// multiplied by 1/(n-1) in FP64 and rounded once to FP32.
 // PALD_ACCUM_PLAIN keeps one FP32 running sum (the precision baseline).
 #pragma once
 
@@ -37,9 +41,12 @@
 
 namespace pald {
 
+constexpr int kMergeEvery = 4;      // y per FP32 partial
+constexpr float kMergeBias = 4.0f;  // >= kMergeEvery * 1/2 + carried error
+
 template <int BM, int G>
 struct CohesionGeom {
-  static constexpr int BK = 16;                // y per stage (= compensation chunk)
+  static constexpr int BK = 16;                // y per pipeline stage
   static constexpr int TPD = BM / (4 * G);
   static constexpr int NT = TPD * TPD;
   static constexpr int TM = 4 * G;
@@ -62,68 +69,65 @@ __device__ __forceinline__ void tie_constants(float b, float& s, float& c) {
   c = __fsub_rn(0.5f, __fmul_rn(b, s));  // b*s is exact (power-of-two scaling)
 }
 
-// One (x, z, y) step; see the header comment.
-__device__ __forceinline__ void cohesion_step(float& sxz, float& szx, float a1, float a2, float b, float s, float c,
-                                              float r1, float r2) {
-  asm("{\n\t.reg .pred p;\n\t.reg .f32 m, v1, v2;\n\t"
-      "min.f32 m, %2, %3;\n\t"
-      "setp.ge.f32 p, m, %4;\n\t"
-      "fma.rn.sat.f32 v2, %3, %5, %6;\n\t"
-      "fma.rn.sat.f32 v1, %2, %5, %6;\n\t"
-      "@p fma.rn.f32 %0, v2, %7, %0;\n\t"
-      "@p fma.rn.f32 %1, v1, %8, %1;\n\t}"
-      : "+f"(sxz), "+f"(szx)
+// One (x, z, y) step on the packed partial {S_xz, S_zx}; see the header.
+__device__ __forceinline__ void cohesion_step(uint64_t& sacc, float a1, float a2, float b, float s, float c, float r1,
+                                              float r2) {
+  asm("{\n\t.reg .pred p;\n\t.reg .f32 m, v1, v2, sx, sz;\n\t"
+      "mov.b64 {sx, sz}, %0;\n\t"
+      "min.f32 m, %1, %2;\n\t"
+      "setp.ge.f32 p, m, %3;\n\t"
+      "fma.rn.sat.f32 v2, %2, %4, %5;\n\t"
+      "fma.rn.sat.f32 v1, %1, %4, %5;\n\t"
+      "@p fma.rn.f32 sx, v2, %6, sx;\n\t"
+      "@p fma.rn.f32 sz, v1, %7, sz;\n\t"
+      "mov.b64 %0, {sx, sz};\n\t}"
+      : "+l"(sacc)
       : "f"(a1), "f"(a2), "f"(b), "f"(s), "f"(c), "f"(r1), "f"(r2));
 }
 
-// Error-free TwoSum: h + e == old h + old e exactly; e carries the error.
-__device__ __forceinline__ void two_sum_fold(float& h, float& e) {
-  const float s = __fadd_rn(h, e);
-  const float bb = __fsub_rn(s, h);
-  const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(e, bb));
-  h = s;
-  e = err;
+// Fast2Sum on both lanes: h + s == old h + old s exactly when |h| >= |s|.
+__device__ __forceinline__ void fast2sum_fold(uint64_t& h, uint64_t& s) {
+  asm("{\n\t.reg .b64 t, z;\n\t"
+      "add.rn.f32x2 t, %0, %1;\n\t"
+      "sub.rn.f32x2 z, t, %0;\n\t"
+      "sub.rn.f32x2 %1, %1, z;\n\t"
+      "mov.b64 %0, t;\n\t}"
+      : "+l"(h), "+l"(s));
 }
 
-// r = 1/u for the staged u values of this stage; 0 on the diagonal (y == x)
-// and outside the matrix (where u was zero-filled).
-template <int BM, int NT, int BK>
-__device__ __forceinline__ void reciprocal_stage(float* buf, int64_t y0, int64_t c0) {
-  uint32_t* ub = reinterpret_cast<uint32_t*>(buf);
-#pragma unroll
-  for (int k = threadIdx.x; k < BK * BM; k += NT) {
-    const int r = k / BM, cc = k % BM;
-    const int u = static_cast<int>(ub[k]);
-    const bool zero = (u <= 0) || (y0 + r == c0 + cc);
-    buf[k] = zero ? 0.f : __frcp_rn(static_cast<float>(u));
-  }
+__device__ __forceinline__ uint64_t pack2(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
 template <int BM, int G, int MODE>
-__device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const int32_t* __restrict__ U, int64_t n,
+__device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const float* __restrict__ R, int64_t n,
                                               float* __restrict__ C, int bi, int bj, float* smem) {
   using Geo = CohesionGeom<BM, G>;
   constexpr int BK = Geo::BK, TM = Geo::TM, TPD = Geo::TPD, NT = Geo::NT;
   const int64_t X0 = static_cast<int64_t>(bi) * BM, Z0 = static_cast<int64_t>(bj) * BM;
   const int tx = threadIdx.x % TPD, tz = threadIdx.x / TPD;
   const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(D) % 16) == 0 &&
-                   (reinterpret_cast<uintptr_t>(U) % 16) == 0;
+                   (reinterpret_cast<uintptr_t>(R) % 16) == 0;
 
   float* Ad = smem;                   // [2][BK][BM]  d_xy  (row y, column x)
-  float* Ar = smem + 2 * Geo::STAGE;  // [2][BK][BM]  u_xy -> r_xy
+  float* Ar = smem + 2 * Geo::STAGE;  // [2][BK][BM]  r_xy
   float* Bd = smem + 4 * Geo::STAGE;  // [2][BK][BM]  d_zy
-  float* Br = smem + 6 * Geo::STAGE;  // [2][BK][BM]  u_zy -> r_zy
-  const float* Uf = reinterpret_cast<const float*>(U);
+  float* Br = smem + 6 * Geo::STAGE;  // [2][BK][BM]  r_zy
 
   const int64_t nstages = (n + BK - 1) / BK;
   stage_rows<BM, NT, BK>(Ad, D, n, 0, X0, vec);
-  stage_rows<BM, NT, BK>(Ar, Uf, n, 0, X0, vec);
+  stage_rows<BM, NT, BK>(Ar, R, n, 0, X0, vec);
   stage_rows<BM, NT, BK>(Bd, D, n, 0, Z0, vec);
-  stage_rows<BM, NT, BK>(Br, Uf, n, 0, Z0, vec);
+  stage_rows<BM, NT, BK>(Br, R, n, 0, Z0, vec);
   cp_async_commit();
 
   float bv[TM][TM], sv[TM][TM], cv[TM][TM];
-  float sxz[TM][TM], szx[TM][TM], hxz[TM][TM], hzx[TM][TM];
+  uint64_t sacc[TM][TM], hacc[TM][TM];
 #pragma unroll
   for (int gi = 0; gi < G; ++gi)
 #pragma unroll
@@ -141,33 +145,35 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
         }
       }
     }
+  const uint64_t zero2 = pack2(0.f, 0.f);
+  const uint64_t bias2 = pack2(kMergeBias, kMergeBias);
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TM; ++j) sxz[i][j] = szx[i][j] = hxz[i][j] = hzx[i][j] = 0.f;
+    for (int j = 0; j < TM; ++j) {
+      sacc[i][j] = zero2;
+      hacc[i][j] = bias2;
+    }
 
   for (int64_t st = 0; st < nstages; ++st) {
     const int buf = static_cast<int>(st & 1);
     if (st + 1 < nstages) {
       const int nb = (buf ^ 1) * Geo::STAGE;
       stage_rows<BM, NT, BK>(Ad + nb, D, n, (st + 1) * BK, X0, vec);
-      stage_rows<BM, NT, BK>(Ar + nb, Uf, n, (st + 1) * BK, X0, vec);
+      stage_rows<BM, NT, BK>(Ar + nb, R, n, (st + 1) * BK, X0, vec);
       stage_rows<BM, NT, BK>(Bd + nb, D, n, (st + 1) * BK, Z0, vec);
-      stage_rows<BM, NT, BK>(Br + nb, Uf, n, (st + 1) * BK, Z0, vec);
+      stage_rows<BM, NT, BK>(Br + nb, R, n, (st + 1) * BK, Z0, vec);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    reciprocal_stage<BM, NT, BK>(Ar + buf * Geo::STAGE, st * BK, X0);
-    reciprocal_stage<BM, NT, BK>(Br + buf * Geo::STAGE, st * BK, Z0);
-    __syncthreads();
     const float* ad = Ad + buf * Geo::STAGE;
     const float* ar = Ar + buf * Geo::STAGE;
     const float* bd = Bd + buf * Geo::STAGE;
     const float* br = Br + buf * Geo::STAGE;
-#pragma unroll 2
+#pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
       float a1[TM], r1[TM], a2[TM], r2[TM];
 #pragma unroll
@@ -186,23 +192,27 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
       for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < TM; ++j)
-          cohesion_step(sxz[i][j], szx[i][j], a1[i], a2[j], bv[i][j], sv[i][j], cv[i][j], r1[i], r2[j]);
-    }
-    if (MODE == PALD_ACCUM_COMPENSATED) {
+          cohesion_step(sacc[i][j], a1[i], a2[j], bv[i][j], sv[i][j], cv[i][j], r1[i], r2[j]);
+      if (MODE == PALD_ACCUM_COMPENSATED && (kk % kMergeEvery) == kMergeEvery - 1) {
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+        for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TM; ++j) {
-          two_sum_fold(hxz[i][j], sxz[i][j]);
-          two_sum_fold(hzx[i][j], szx[i][j]);
-        }
+          for (int j = 0; j < TM; ++j) fast2sum_fold(hacc[i][j], sacc[i][j]);
+      }
     }
     __syncthreads();
   }
 
   const double inv = 1.0 / static_cast<double>(n - 1);
-  auto finish = [&](float h, float s) -> float {
-    if (MODE == PALD_ACCUM_COMPENSATED) return static_cast<float>((static_cast<double>(h) + static_cast<double>(s)) * inv);
+  // value of the (xz or zx) lane: compensated (H - B) + S in FP64, or plain S
+  auto finish = [&](uint64_t h2, uint64_t s2, bool zx) -> float {
+    float hl, hh, sl, sh;
+    unpack2(h2, hl, hh);
+    unpack2(s2, sl, sh);
+    const float h = zx ? hh : hl, s = zx ? sh : sl;
+    if (MODE == PALD_ACCUM_COMPENSATED)
+      return static_cast<float>(((static_cast<double>(h) - static_cast<double>(kMergeBias)) +
+                                 static_cast<double>(s)) * inv);
     return static_cast<float>(static_cast<double>(s) * inv);
   };
 #pragma unroll
@@ -216,8 +226,9 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
       for (int gj = 0; gj < G; ++gj) {
         const int q = gj * 4;
         const int64_t z = Z0 + gj * (BM / G) + 4 * tz;
-        float4 v = make_float4(finish(hxz[r][q], sxz[r][q]), finish(hxz[r][q + 1], sxz[r][q + 1]),
-                               finish(hxz[r][q + 2], sxz[r][q + 2]), finish(hxz[r][q + 3], sxz[r][q + 3]));
+        float4 v = make_float4(finish(hacc[r][q], sacc[r][q], false), finish(hacc[r][q + 1], sacc[r][q + 1], false),
+                               finish(hacc[r][q + 2], sacc[r][q + 2], false),
+                               finish(hacc[r][q + 3], sacc[r][q + 3], false));
         float* p = C + x * n + z;
         if (vec && z + 3 < n) {
           *reinterpret_cast<float4*>(p) = v;
@@ -241,8 +252,9 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
         for (int gi = 0; gi < G; ++gi) {
           const int r = gi * 4;
           const int64_t x = X0 + gi * (BM / G) + 4 * tx;
-          float4 v = make_float4(finish(hzx[r][q], szx[r][q]), finish(hzx[r + 1][q], szx[r + 1][q]),
-                                 finish(hzx[r + 2][q], szx[r + 2][q]), finish(hzx[r + 3][q], szx[r + 3][q]));
+          float4 v = make_float4(finish(hacc[r][q], sacc[r][q], true), finish(hacc[r + 1][q], sacc[r + 1][q], true),
+                                 finish(hacc[r + 2][q], sacc[r + 2][q], true),
+                                 finish(hacc[r + 3][q], sacc[r + 3][q], true));
           float* p = C + z * n + x;
           if (vec && x + 3 < n) {
             *reinterpret_cast<float4*>(p) = v;
@@ -254,6 +266,32 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
           }
         }
       }
+  }
+}
+
+// R[row][col] = 1/u (correctly rounded FP32), 0 on the diagonal and where
+// u <= 0; rows [r0, r1) of one n x n matrix, one warp per row stretch.
+__device__ __forceinline__ void reciprocal_rows(const int32_t* __restrict__ U, float* __restrict__ R, int64_t n,
+                                                int64_t row, bool vec) {
+  const int32_t* u = U + row * n;
+  float* r = R + row * n;
+  if (vec) {
+    const int64_t n4 = n / 4;
+    for (int64_t k = threadIdx.x; k < n4; k += blockDim.x) {
+      const int4 q = __ldg(reinterpret_cast<const int4*>(u) + k);
+      const int64_t c = 4 * k;
+      float4 o;
+      o.x = (q.x <= 0 || c + 0 == row) ? 0.f : __frcp_rn(static_cast<float>(q.x));
+      o.y = (q.y <= 0 || c + 1 == row) ? 0.f : __frcp_rn(static_cast<float>(q.y));
+      o.z = (q.z <= 0 || c + 2 == row) ? 0.f : __frcp_rn(static_cast<float>(q.z));
+      o.w = (q.w <= 0 || c + 3 == row) ? 0.f : __frcp_rn(static_cast<float>(q.w));
+      reinterpret_cast<float4*>(r)[k] = o;
+    }
+  } else {
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
+      const int32_t q = __ldg(u + c);
+      r[c] = (q <= 0 || c == row) ? 0.f : __frcp_rn(static_cast<float>(q));
+    }
   }
 }
 

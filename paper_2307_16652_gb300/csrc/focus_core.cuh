@@ -8,8 +8,14 @@
 //     sat(m*s + c) = sat((m - t)*s) = [m > t]   exactly,
 // because m > t implies m - t >= ulp(t) >= 2^(e-23), and t*s is a pure
 // power-of-two scaling, so no rounding can move the result across 0 or 1.
-// The min is one FMNMX on the ALU pipe, the step and the sum two ops on the
-// FMA pipe: the inner loop keeps both pipes busy.
+//
+// Two consecutive z are handled together:
+//     m0 = min(d_xz0, d_yz0), m1 = min(d_xz1, d_yz1)     2 x FMNMX   (ALU pipe)
+//     h0 = sat(m0*s + c),     h1 = sat(m1*s + c)         2 x FFMA    (FMA pipe)
+//     {acc0, acc1} += {h0, h1}                           1 x FADD2   (FMA pipe, 2 cycles)
+// i.e. 2.5 issue slots per (x, y, z) with the ALU and FMA pipes equally
+// loaded (4 cycles each per two z).  The two partial counts are exact
+// integers in FP32 (n < 2^24) and are added at the end.
 //
 // Layout: the CTA streams z through shared memory in chunks of BK.  Because
 // D is symmetric, column block D[X, z-chunk] is read as rows D[z-chunk, X],
@@ -94,6 +100,25 @@ __device__ __forceinline__ void store4i(int32_t* __restrict__ M, int64_t n, int6
   if (col + 3 < n) p[3] = v.w;
 }
 
+// {acc0, acc1} += {[min(a0, b0) > t], [min(a1, b1) > t]} for two consecutive z.
+__device__ __forceinline__ void focus_step2(uint64_t& acc, float a0, float b0, float a1, float b1, float s, float c) {
+  asm("{\n\t.reg .f32 m0, m1, h0, h1;\n\t.reg .b64 hh;\n\t"
+      "min.f32 m0, %1, %2;\n\t"
+      "min.f32 m1, %3, %4;\n\t"
+      "fma.rn.sat.f32 h0, m0, %5, %6;\n\t"
+      "fma.rn.sat.f32 h1, m1, %5, %6;\n\t"
+      "mov.b64 hh, {h0, h1};\n\t"
+      "add.rn.f32x2 %0, %0, hh;\n\t}"
+      : "+l"(acc)
+      : "f"(a0), "f"(b0), "f"(a1), "f"(b1), "f"(s), "f"(c));
+}
+
+__device__ __forceinline__ int count_of(uint64_t acc) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc));
+  return static_cast<int>(lo) + static_cast<int>(hi);
+}
+
 // Computes and stores U[X, Y] (and U[Y, X] when bi != bj) for tile (bi, bj).
 // `smem` holds Geom::SMEM_FLOATS floats.  Must be called by all NT threads.
 template <int BM, int G>
@@ -115,7 +140,7 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
 
   // thresholds t = d_xy -> c = -t * scale (exact: power-of-two scaling)
   float cst[TM][TM];
-  float acc[TM][TM];
+  uint64_t acc[TM][TM];
 #pragma unroll
   for (int gi = 0; gi < G; ++gi)
 #pragma unroll
@@ -133,7 +158,7 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < TM; ++j) acc[i][j] = 0.f;
+    for (int j = 0; j < TM; ++j) acc[i][j] = 0ull;
 
   for (int64_t st = 0; st < nstages; ++st) {
     const int buf = static_cast<int>(st & 1);
@@ -148,20 +173,24 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
     __syncthreads();
     const float* as = As + buf * Geo::STAGE;
     const float* bs = Bs + buf * Geo::STAGE;
-#pragma unroll 2
-    for (int kk = 0; kk < BK; ++kk) {
-      float a[TM], b[TM];
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 2) {
+      float a0[TM], b0[TM], a1[TM], b1[TM];
 #pragma unroll
       for (int g = 0; g < G; ++g) {
-        const float4 va = *reinterpret_cast<const float4*>(as + kk * BM + g * (BM / G) + 4 * tx);
-        const float4 vb = *reinterpret_cast<const float4*>(bs + kk * BM + g * (BM / G) + 4 * ty);
-        a[4 * g + 0] = va.x; a[4 * g + 1] = va.y; a[4 * g + 2] = va.z; a[4 * g + 3] = va.w;
-        b[4 * g + 0] = vb.x; b[4 * g + 1] = vb.y; b[4 * g + 2] = vb.z; b[4 * g + 3] = vb.w;
+        const float4 va0 = *reinterpret_cast<const float4*>(as + kk * BM + g * (BM / G) + 4 * tx);
+        const float4 vb0 = *reinterpret_cast<const float4*>(bs + kk * BM + g * (BM / G) + 4 * ty);
+        const float4 va1 = *reinterpret_cast<const float4*>(as + (kk + 1) * BM + g * (BM / G) + 4 * tx);
+        const float4 vb1 = *reinterpret_cast<const float4*>(bs + (kk + 1) * BM + g * (BM / G) + 4 * ty);
+        a0[4 * g + 0] = va0.x; a0[4 * g + 1] = va0.y; a0[4 * g + 2] = va0.z; a0[4 * g + 3] = va0.w;
+        b0[4 * g + 0] = vb0.x; b0[4 * g + 1] = vb0.y; b0[4 * g + 2] = vb0.z; b0[4 * g + 3] = vb0.w;
+        a1[4 * g + 0] = va1.x; a1[4 * g + 1] = va1.y; a1[4 * g + 2] = va1.z; a1[4 * g + 3] = va1.w;
+        b1[4 * g + 0] = vb1.x; b1[4 * g + 1] = vb1.y; b1[4 * g + 2] = vb1.z; b1[4 * g + 3] = vb1.w;
       }
 #pragma unroll
       for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < TM; ++j) acc[i][j] += ffma_sat(fmin_(a[i], b[j]), scale, cst[i][j]);
+        for (int j = 0; j < TM; ++j) focus_step2(acc[i][j], a0[i], b0[j], a1[i], b1[j], scale, cst[i][j]);
     }
     __syncthreads();
   }
@@ -177,8 +206,8 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
 #pragma unroll
       for (int gj = 0; gj < G; ++gj) {
         const int c = gj * 4;
-        int4 v = make_int4(nn - static_cast<int>(acc[r][c + 0]), nn - static_cast<int>(acc[r][c + 1]),
-                           nn - static_cast<int>(acc[r][c + 2]), nn - static_cast<int>(acc[r][c + 3]));
+        int4 v = make_int4(nn - count_of(acc[r][c + 0]), nn - count_of(acc[r][c + 1]),
+                           nn - count_of(acc[r][c + 2]), nn - count_of(acc[r][c + 3]));
         store4i(U, n, x, Y0 + gj * (BM / G) + 4 * ty, v, vec);
       }
     }
@@ -192,8 +221,8 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
 #pragma unroll
         for (int gi = 0; gi < G; ++gi) {
           const int r = gi * 4;
-          int4 v = make_int4(nn - static_cast<int>(acc[r + 0][c]), nn - static_cast<int>(acc[r + 1][c]),
-                             nn - static_cast<int>(acc[r + 2][c]), nn - static_cast<int>(acc[r + 3][c]));
+          int4 v = make_int4(nn - count_of(acc[r + 0][c]), nn - count_of(acc[r + 1][c]),
+                             nn - count_of(acc[r + 2][c]), nn - count_of(acc[r + 3][c]));
           store4i(U, n, y, X0 + gi * (BM / G) + 4 * tx, v, vec);
         }
       }

@@ -96,15 +96,19 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
   if (!D || !U || !C || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
   const pald_opts o = opts_or_default(opts);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // scratch: the scan summary (validation only) and R = 1/u, n x n FP32
+  const size_t rbytes = static_cast<size_t>(n) * static_cast<size_t>(n) * sizeof(float);
+  Scratch scratch(s);
+  cudaError_t e = scratch.alloc(rbytes + 256);
+  if (e != cudaSuccess) return cuda_fail(e);
+  float* R = static_cast<float*>(scratch.p);
   if (o.validate) {
-    Scratch scratch(s);
-    cudaError_t e = scratch.alloc(sizeof(ScanResult));
-    if (e != cudaSuccess) return cuda_fail(e);
-    pald_status st = scan_and_check(D, n, static_cast<ScanResult*>(scratch.p), true, s);
+    auto* scan = reinterpret_cast<ScanResult*>(static_cast<char*>(scratch.p) + rbytes);
+    pald_status st = scan_and_check(D, n, scan, true, s);
     if (st != PALD_OK) return st;
   }
-  cudaError_t e = launch_cohesion(D, U, n, C, o.accum_mode, o.schedule_id, s);
-  if (e != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_reciprocal(U, R, n, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_cohesion(D, R, n, C, o.accum_mode, o.schedule_id, s)) != cudaSuccess) return cuda_fail(e);
   return PALD_OK;
 }
 
@@ -156,8 +160,8 @@ int32_t pald_schedule_count(void) { return 2; }
 
 const char* pald_schedule_name(int32_t id) {
   switch (id) {
-    case 0: return "focus 128x128 tiles (8x8 per thread) / cohesion 64x64 tiles (4x4 per thread)";
-    case 1: return "focus 64x64 tiles (4x4 per thread) / cohesion 32x32 tiles (4x4 per thread)";
+    case 0: return "focus 64x64 tiles / cohesion 64x64 tiles (4x4 pairs per thread)";
+    case 1: return "focus 32x32 tiles / cohesion 32x32 tiles (4x4 pairs per thread)";
     default: return nullptr;
   }
 }

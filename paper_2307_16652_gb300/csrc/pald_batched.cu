@@ -68,7 +68,7 @@ __device__ __forceinline__ int64_t next_item(int* counter, int* slot) {
   return *slot;
 }
 
-__global__ void __launch_bounds__(FG::NT) batched_focus_kernel(const float* __restrict__ D, int32_t* __restrict__ U,
+__global__ void __launch_bounds__(FG::NT, 2) batched_focus_kernel(const float* __restrict__ D, int32_t* __restrict__ U,
                                                                const MatrixDesc* __restrict__ mats,
                                                                const ScanResult* __restrict__ scans,
                                                                const WorkItem* __restrict__ items, int64_t n_items,
@@ -85,9 +85,17 @@ __global__ void __launch_bounds__(FG::NT) batched_focus_kernel(const float* __re
   }
 }
 
+// R = 1/u for every matrix (zero diagonal): blockIdx.y = matrix.
+__global__ void __launch_bounds__(256) batched_reciprocal_kernel(const int32_t* __restrict__ U, float* __restrict__ R,
+                                                                 const MatrixDesc* __restrict__ mats) {
+  const MatrixDesc md = mats[blockIdx.y];
+  const bool vec = (md.n % 4) == 0;  // offsets are multiples of 4 elements
+  for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x) reciprocal_rows(U + md.off, R + md.off, md.n, row, vec);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(CG::NT) batched_cohesion_kernel(const float* __restrict__ D,
-                                                                  const int32_t* __restrict__ U,
+                                                                  const float* __restrict__ R,
                                                                   float* __restrict__ C,
                                                                   const MatrixDesc* __restrict__ mats,
                                                                   const WorkItem* __restrict__ items,
@@ -99,7 +107,7 @@ __global__ void __launch_bounds__(CG::NT) batched_cohesion_kernel(const float* _
     if (it >= n_items) break;
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
-    cohesion_tile<kBC, 1, MODE>(D + md.off, U + md.off, md.n, C + md.off, w.bi, w.bj, smem);
+    cohesion_tile<kBC, 1, MODE>(D + md.off, R + md.off, md.n, C + md.off, w.bi, w.bj, smem);
   }
 }
 
@@ -179,7 +187,10 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   const size_t o_fitems = align_up(o_scans + sizeof(ScanResult) * count, 256);
   const size_t o_citems = align_up(o_fitems + sizeof(WorkItem) * fitems.size(), 256);
   const size_t o_counters = align_up(o_citems + sizeof(WorkItem) * citems.size(), 256);
-  const size_t total = o_counters + 256;
+  int64_t r_elems = 0;  // R uses the same offsets as D, U and C
+  for (int i = 0; i < count; ++i) r_elems = std::max<int64_t>(r_elems, offs[i] + ns[i] * ns[i]);
+  const size_t o_recip = align_up(o_counters + 256, 256);
+  const size_t total = o_recip + sizeof(float) * static_cast<size_t>(r_elems);
 
   Plan p;
   p.device = device;
@@ -191,6 +202,7 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   auto* d_fitems = reinterpret_cast<WorkItem*>(base + o_fitems);
   auto* d_citems = reinterpret_cast<WorkItem*>(base + o_citems);
   auto* d_counters = reinterpret_cast<int*>(base + o_counters);
+  auto* d_recip = reinterpret_cast<float*>(base + o_recip);
   e = cudaMemcpy(d_mats, mats.data(), sizeof(MatrixDesc) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_fitems, fitems.data(), sizeof(WorkItem) * fitems.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_citems, citems.data(), sizeof(WorkItem) * citems.size(), cudaMemcpyHostToDevice);
@@ -220,12 +232,13 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     batched_scan_kernel<<<dim3(kScanBlocksPerMatrix, count), 256, 0, cs>>>(D, d_mats, d_scans);
     batched_focus_kernel<<<gf, FG::NT, 0, cs>>>(D, U, d_mats, d_scans, d_fitems,
                                                 static_cast<int64_t>(fitems.size()), d_counters);
+    batched_reciprocal_kernel<<<dim3(8, count), 256, 0, cs>>>(U, d_recip, d_mats);
     if (plain)
       batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, 0, cs>>>(
-          D, U, C, d_mats, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
+          D, d_recip, C, d_mats, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
     else
       batched_cohesion_kernel<PALD_ACCUM_COMPENSATED><<<gc, CG::NT, 0, cs>>>(
-          D, U, C, d_mats, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
+          D, d_recip, C, d_mats, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
     cudaError_t launch_err = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &p.graph);
     if (e == cudaSuccess && launch_err != cudaSuccess) e = launch_err;

@@ -101,8 +101,9 @@ __host__ __device__ __forceinline__ void tri_decode(int64_t t, int64_t T, int* b
 cudaError_t launch_scan(const float* D, int64_t n, ScanResult* out, bool validate, cudaStream_t s);
 cudaError_t launch_focus(const float* D, int64_t n, int32_t* U, const ScanResult* scan, int schedule,
                          cudaStream_t s);
-cudaError_t launch_cohesion(const float* D, const int32_t* U, int64_t n, float* C, int accum_mode,
-                            int schedule, cudaStream_t s);
+cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_t s);
+cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, int accum_mode, int schedule,
+                            cudaStream_t s);
 
 // Batched: descriptors of every matrix, and a flat list of tile work items.
 struct MatrixDesc {
@@ -119,7 +120,6 @@ struct WorkItem {
 };
 
 // Tile edge of each pass (elements).
-constexpr int kFocusTile = 128;
 constexpr int kCohesionTile = 64;
 constexpr int kBatchedFocusTile = 64;
 constexpr int kBatchedCohesionTile = 64;
