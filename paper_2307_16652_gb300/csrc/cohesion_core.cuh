@@ -1,4 +1,4 @@
-// Pass 2 core: cohesion of one BM x BM tile pair (X, Z), X <= Z.
+// Pass 2 core: cohesion of one CTA tile of the pair of blocks (X, Z), X <= Z.
 //
 // For an output pair (x, z) and every third point y the paper's cohesion
 // (Sec. 2 eq. (cohesion), written out as eq. (fxz)) with the half-credit tie
@@ -44,14 +44,9 @@ namespace pald {
 constexpr int kMergeEvery = 4;      // y per FP32 partial
 constexpr float kMergeBias = 4.0f;  // >= kMergeEvery * 1/2 + carried error
 
-template <int BM, int G>
-struct CohesionGeom {
-  static constexpr int BK = 16;                // y per pipeline stage
-  static constexpr int TPD = BM / (4 * G);
-  static constexpr int NT = TPD * TPD;
-  static constexpr int TM = 4 * G;
-  static constexpr int STAGE = BK * BM;        // floats per operand per stage
-  static constexpr int SMEM_FLOATS = 2 * 4 * STAGE;  // two stages of D_X, R_X, D_Z, R_Z
+template <class Geo>
+struct CohesionSmem {
+  static constexpr int FLOATS = 2 * 2 * (Geo::SX + Geo::SY);  // two stages of D_X, R_X, D_Z, R_Z
 };
 
 __device__ __forceinline__ void tie_constants(float b, float& s, float& c) {
@@ -104,53 +99,50 @@ __device__ __forceinline__ void unpack2(uint64_t v, float& lo, float& hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-template <int BM, int G, int MODE>
+// Computes C[X, Z] (and C[Z, X] off the diagonal) for super-tile (bi, bj),
+// column slice `slice`.  `smem` holds CohesionSmem<Geo>::FLOATS floats.
+// Must be called by all Geo::NT threads.
+template <class Geo, int MODE>
 __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const float* __restrict__ R, int64_t n,
-                                              float* __restrict__ C, int bi, int bj, float* smem) {
-  using Geo = CohesionGeom<BM, G>;
-  constexpr int BK = Geo::BK, TM = Geo::TM, TPD = Geo::TPD, NT = Geo::NT;
-  const int64_t X0 = static_cast<int64_t>(bi) * BM, Z0 = static_cast<int64_t>(bj) * BM;
-  const int tx = threadIdx.x % TPD, tz = threadIdx.x / TPD;
+                                              float* __restrict__ C, int bi, int bj, int slice, float* smem) {
+  constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY, NT = Geo::NT;
+  static_assert(BK % kMergeEvery == 0, "stages must hold whole merge chunks");
+  const int64_t X0 = static_cast<int64_t>(bi) * Geo::B;
+  const int64_t Z0 = static_cast<int64_t>(bj) * Geo::B + static_cast<int64_t>(slice) * Geo::BY;
+  const int tx = threadIdx.x % Geo::TPX, tz = threadIdx.x / Geo::TPX;
   const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(D) % 16) == 0 &&
                    (reinterpret_cast<uintptr_t>(R) % 16) == 0;
 
-  float* Ad = smem;                   // [2][BK][BM]  d_xy  (row y, column x)
-  float* Ar = smem + 2 * Geo::STAGE;  // [2][BK][BM]  r_xy
-  float* Bd = smem + 4 * Geo::STAGE;  // [2][BK][BM]  d_zy
-  float* Br = smem + 6 * Geo::STAGE;  // [2][BK][BM]  r_zy
+  float* Ad = smem;                                   // [2][BK][BX]  d_xy  (row y, column x)
+  float* Ar = Ad + 2 * Geo::SX;                       // [2][BK][BX]  r_xy
+  float* Bd = Ar + 2 * Geo::SX;                       // [2][BK][BY]  d_zy
+  float* Br = Bd + 2 * Geo::SY;                       // [2][BK][BY]  r_zy
 
   const int64_t nstages = (n + BK - 1) / BK;
-  stage_rows<BM, NT, BK>(Ad, D, n, 0, X0, vec);
-  stage_rows<BM, NT, BK>(Ar, R, n, 0, X0, vec);
-  stage_rows<BM, NT, BK>(Bd, D, n, 0, Z0, vec);
-  stage_rows<BM, NT, BK>(Br, R, n, 0, Z0, vec);
+  stage_rows<Geo::BX, NT, BK>(Ad, D, n, 0, X0, vec);
+  stage_rows<Geo::BX, NT, BK>(Ar, R, n, 0, X0, vec);
+  stage_rows<Geo::BY, NT, BK>(Bd, D, n, 0, Z0, vec);
+  stage_rows<Geo::BY, NT, BK>(Br, R, n, 0, Z0, vec);
   cp_async_commit();
 
-  float bv[TM][TM], sv[TM][TM], cv[TM][TM];
-  uint64_t sacc[TM][TM], hacc[TM][TM];
+  float bv[TX][TY], sv[TX][TY], cv[TX][TY];
+  uint64_t sacc[TX][TY], hacc[TX][TY];
 #pragma unroll
-  for (int gi = 0; gi < G; ++gi)
+  for (int i = 0; i < TX; ++i) {
+    const int64_t x = X0 + Geo::row_off(tx, i);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t x = X0 + gi * (BM / G) + 4 * tx + i;
-#pragma unroll
-      for (int gj = 0; gj < G; ++gj) {
-        const float4 t = load4(D, n, x, Z0 + gj * (BM / G) + 4 * tz, vec);
-        const float tv[4] = {t.x, t.y, t.z, t.w};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int r = gi * 4 + i, q = gj * 4 + j;
-          bv[r][q] = tv[j];
-          tie_constants(tv[j], sv[r][q], cv[r][q]);
-        }
-      }
+    for (int j = 0; j < TY; ++j) {
+      const int64_t z = Z0 + Geo::col_off(tz, j);
+      bv[i][j] = (x < n && z < n) ? __ldg(D + x * n + z) : 0.f;
+      tie_constants(bv[i][j], sv[i][j], cv[i][j]);
     }
+  }
   const uint64_t zero2 = pack2(0.f, 0.f);
   const uint64_t bias2 = pack2(kMergeBias, kMergeBias);
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
+  for (int i = 0; i < TX; ++i)
 #pragma unroll
-    for (int j = 0; j < TM; ++j) {
+    for (int j = 0; j < TY; ++j) {
       sacc[i][j] = zero2;
       hacc[i][j] = bias2;
     }
@@ -158,46 +150,44 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
   for (int64_t st = 0; st < nstages; ++st) {
     const int buf = static_cast<int>(st & 1);
     if (st + 1 < nstages) {
-      const int nb = (buf ^ 1) * Geo::STAGE;
-      stage_rows<BM, NT, BK>(Ad + nb, D, n, (st + 1) * BK, X0, vec);
-      stage_rows<BM, NT, BK>(Ar + nb, R, n, (st + 1) * BK, X0, vec);
-      stage_rows<BM, NT, BK>(Bd + nb, D, n, (st + 1) * BK, Z0, vec);
-      stage_rows<BM, NT, BK>(Br + nb, R, n, (st + 1) * BK, Z0, vec);
+      const int64_t y0 = (st + 1) * BK;
+      stage_rows<Geo::BX, NT, BK>(Ad + (buf ^ 1) * Geo::SX, D, n, y0, X0, vec);
+      stage_rows<Geo::BX, NT, BK>(Ar + (buf ^ 1) * Geo::SX, R, n, y0, X0, vec);
+      stage_rows<Geo::BY, NT, BK>(Bd + (buf ^ 1) * Geo::SY, D, n, y0, Z0, vec);
+      stage_rows<Geo::BY, NT, BK>(Br + (buf ^ 1) * Geo::SY, R, n, y0, Z0, vec);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const float* ad = Ad + buf * Geo::STAGE;
-    const float* ar = Ar + buf * Geo::STAGE;
-    const float* bd = Bd + buf * Geo::STAGE;
-    const float* br = Br + buf * Geo::STAGE;
+    const float* ad = Ad + buf * Geo::SX;
+    const float* ar = Ar + buf * Geo::SX;
+    const float* bd = Bd + buf * Geo::SY;
+    const float* br = Br + buf * Geo::SY;
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      float a1[TM], r1[TM], a2[TM], r2[TM];
+      float a1[TX], r1[TX], a2[TY], r2[TY];
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int ox = kk * BM + g * (BM / G) + 4 * tx, oz = kk * BM + g * (BM / G) + 4 * tz;
-        const float4 va = *reinterpret_cast<const float4*>(ad + ox);
-        const float4 vr = *reinterpret_cast<const float4*>(ar + ox);
-        const float4 vb = *reinterpret_cast<const float4*>(bd + oz);
-        const float4 vs = *reinterpret_cast<const float4*>(br + oz);
-        a1[4 * g + 0] = va.x; a1[4 * g + 1] = va.y; a1[4 * g + 2] = va.z; a1[4 * g + 3] = va.w;
-        r1[4 * g + 0] = vr.x; r1[4 * g + 1] = vr.y; r1[4 * g + 2] = vr.z; r1[4 * g + 3] = vr.w;
-        a2[4 * g + 0] = vb.x; a2[4 * g + 1] = vb.y; a2[4 * g + 2] = vb.z; a2[4 * g + 3] = vb.w;
-        r2[4 * g + 0] = vs.x; r2[4 * g + 1] = vs.y; r2[4 * g + 2] = vs.z; r2[4 * g + 3] = vs.w;
+      for (int g = 0; g < Geo::GX; ++g) {
+        lds<4>(ad + kk * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
+        lds<4>(ar + kk * Geo::BX + Geo::row_off(tx, 4 * g), r1 + 4 * g);
       }
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+      for (int g = 0; g < Geo::GY; ++g) {
+        lds<Geo::CW>(bd + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), a2 + Geo::CW * g);
+        lds<Geo::CW>(br + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), r2 + Geo::CW * g);
+      }
 #pragma unroll
-        for (int j = 0; j < TM; ++j)
+      for (int i = 0; i < TX; ++i)
+#pragma unroll
+        for (int j = 0; j < TY; ++j)
           cohesion_step(sacc[i][j], a1[i], a2[j], bv[i][j], sv[i][j], cv[i][j], r1[i], r2[j]);
       if (MODE == PALD_ACCUM_COMPENSATED && (kk % kMergeEvery) == kMergeEvery - 1) {
 #pragma unroll
-        for (int i = 0; i < TM; ++i)
+        for (int i = 0; i < TX; ++i)
 #pragma unroll
-          for (int j = 0; j < TM; ++j) fast2sum_fold(hacc[i][j], sacc[i][j]);
+          for (int j = 0; j < TY; ++j) fast2sum_fold(hacc[i][j], sacc[i][j]);
       }
     }
     __syncthreads();
@@ -216,56 +206,28 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
     return static_cast<float>(static_cast<double>(s) * inv);
   };
 #pragma unroll
-  for (int gi = 0; gi < G; ++gi)
+  for (int i = 0; i < TX; ++i) {
+    const int64_t x = X0 + Geo::row_off(tx, i);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t x = X0 + gi * (BM / G) + 4 * tx + i;
-      const int r = gi * 4 + i;
-      if (x >= n) continue;
+    for (int gj = 0; gj < Geo::GY; ++gj) {
+      float v[Geo::CW];
 #pragma unroll
-      for (int gj = 0; gj < G; ++gj) {
-        const int q = gj * 4;
-        const int64_t z = Z0 + gj * (BM / G) + 4 * tz;
-        float4 v = make_float4(finish(hacc[r][q], sacc[r][q], false), finish(hacc[r][q + 1], sacc[r][q + 1], false),
-                               finish(hacc[r][q + 2], sacc[r][q + 2], false),
-                               finish(hacc[r][q + 3], sacc[r][q + 3], false));
-        float* p = C + x * n + z;
-        if (vec && z + 3 < n) {
-          *reinterpret_cast<float4*>(p) = v;
-        } else {
-          if (z + 0 < n) p[0] = v.x;
-          if (z + 1 < n) p[1] = v.y;
-          if (z + 2 < n) p[2] = v.z;
-          if (z + 3 < n) p[3] = v.w;
-        }
-      }
+      for (int k = 0; k < Geo::CW; ++k) v[k] = finish(hacc[i][Geo::CW * gj + k], sacc[i][Geo::CW * gj + k], false);
+      storew<Geo::CW>(C, n, x, Z0 + Geo::col_off(tz, Geo::CW * gj), v, vec);
     }
+  }
   if (bi != bj) {
 #pragma unroll
-    for (int gj = 0; gj < G; ++gj)
+    for (int j = 0; j < TY; ++j) {
+      const int64_t z = Z0 + Geo::col_off(tz, j);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t z = Z0 + gj * (BM / G) + 4 * tz + j;
-        const int q = gj * 4 + j;
-        if (z >= n) continue;
+      for (int gi = 0; gi < Geo::GX; ++gi) {
+        float v[4];
 #pragma unroll
-        for (int gi = 0; gi < G; ++gi) {
-          const int r = gi * 4;
-          const int64_t x = X0 + gi * (BM / G) + 4 * tx;
-          float4 v = make_float4(finish(hacc[r][q], sacc[r][q], true), finish(hacc[r + 1][q], sacc[r + 1][q], true),
-                                 finish(hacc[r + 2][q], sacc[r + 2][q], true),
-                                 finish(hacc[r + 3][q], sacc[r + 3][q], true));
-          float* p = C + z * n + x;
-          if (vec && x + 3 < n) {
-            *reinterpret_cast<float4*>(p) = v;
-          } else {
-            if (x + 0 < n) p[0] = v.x;
-            if (x + 1 < n) p[1] = v.y;
-            if (x + 2 < n) p[2] = v.z;
-            if (x + 3 < n) p[3] = v.w;
-          }
-        }
+        for (int k = 0; k < 4; ++k) v[k] = finish(hacc[4 * gi + k][j], sacc[4 * gi + k][j], true);
+        storew<4>(C, n, z, X0 + Geo::row_off(tx, 4 * gi), v, vec);
       }
+    }
   }
 }
 

@@ -1,4 +1,4 @@
-// Pass 1 core: local focus sizes of one BM x BM tile of U.
+// Pass 1 core: local focus sizes of one CTA tile of U.
 //
 // For every pair (x, y) of the tile,
 //     u_xy = #{ z : min(d_xz, d_yz) <= d_xy }                 (Sec. 2, U_xy)
@@ -17,57 +17,40 @@
 // loaded (4 cycles each per two z).  The two partial counts are exact
 // integers in FP32 (n < 2^24) and are added at the end.
 //
-// Layout: the CTA streams z through shared memory in chunks of BK.  Because
-// D is symmetric, column block D[X, z-chunk] is read as rows D[z-chunk, X],
-// so every global read is a contiguous row segment (the "transpose" is
-// free).  Thread (tx, ty) owns x in {g*BM/G + 4*tx + i} and y in
-// {g*BM/G + 4*ty + j} (g < G, i, j < 4): its shared-memory reads are
-// 16-byte vectors with no bank conflicts, and its global stores of u (and of
-// the mirrored tile u_YX) are 16-byte vectors too.
+// Layout: the CTA streams z through shared memory in stages of BK.  Because
+// D is symmetric, the column block D[X, z-stage] is read as the rows
+// D[z-stage, X], so every global read is a contiguous row segment (the
+// "transpose" is free).  See tile_geom.cuh for the thread ownership.
 #pragma once
 
-#include "pald_internal.cuh"
+#include <type_traits>
+
+#include "tile_geom.cuh"
 
 namespace pald {
 
-template <int BM, int G>
-struct FocusGeom {
-  static constexpr int BK = 16;                 // z per pipeline stage
-  static constexpr int TPD = BM / (4 * G);      // threads per tile dimension
-  static constexpr int NT = TPD * TPD;          // threads per CTA
-  static constexpr int TM = 4 * G;              // rows (and columns) per thread
-  static constexpr int STAGE = BK * BM;         // floats per operand per stage
-  static constexpr int SMEM_FLOATS = 2 * 2 * STAGE;
-};
-
-// Copy rows z0..z0+BK-1, columns c0..c0+BM-1 of the n x n matrix at M into
-// dst[BK][BM]; out-of-range elements are zero-filled.
-template <int BM, int NT, int BK>
+// Copy rows z0..z0+BK-1, columns c0..c0+W-1 of the n x n matrix at M into
+// dst[BK][W]; out-of-range elements are zero-filled.
+template <int W, int NT, int BK>
 __device__ __forceinline__ void stage_rows(float* dst, const float* __restrict__ M, int64_t n, int64_t z0,
                                            int64_t c0, bool vec) {
   if (vec) {
-    constexpr int V = BK * BM / 4;
+    constexpr int V = BK * W / 4;
 #pragma unroll
     for (int k = threadIdx.x; k < V; k += NT) {
-      const int r = k / (BM / 4), c = (k % (BM / 4)) * 4;
+      const int r = k / (W / 4), c = (k % (W / 4)) * 4;
       const int64_t row = z0 + r, col = c0 + c;
-      int bytes = 0;
-      const float* src = M;
-      if (row < n && col < n) {
-        const int64_t left = n - col;
-        bytes = left >= 4 ? 16 : static_cast<int>(left) * 4;
-        src = M + row * n + col;
-      }
-      cp_async16(dst + r * BM + c, src, bytes);
+      const bool ok = row < n && col < n;  // n % 4 == 0: a vector is all in or all out
+      cp_async16(dst + r * W + c, ok ? M + row * n + col : M, ok ? 16 : 0);
     }
   } else {
-    constexpr int V = BK * BM;
+    constexpr int V = BK * W;
 #pragma unroll 4
     for (int k = threadIdx.x; k < V; k += NT) {
-      const int r = k / BM, c = k % BM;
+      const int r = k / W, c = k % W;
       const int64_t row = z0 + r, col = c0 + c;
       const bool ok = row < n && col < n;
-      cp_async4(dst + r * BM + c, ok ? M + row * n + col : M, ok ? 4 : 0);
+      cp_async4(dst + r * W + c, ok ? M + row * n + col : M, ok ? 4 : 0);
     }
   }
 }
@@ -86,18 +69,46 @@ __device__ __forceinline__ float4 load4(const float* __restrict__ M, int64_t n, 
   return v;
 }
 
-__device__ __forceinline__ void store4i(int32_t* __restrict__ M, int64_t n, int64_t row, int64_t col, int4 v,
-                                        bool vec) {
+// W (4 or 2) consecutive floats of a shared-memory operand row.
+template <int W = 4>
+__device__ __forceinline__ void lds(const float* p, float* out) {
+  if (W == 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    out[0] = v.x;
+    out[1] = v.y;
+    out[2] = v.z;
+    out[3] = v.w;
+  } else {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    out[0] = v.x;
+    out[1] = v.y;
+  }
+}
+
+// Store W (4 or 2) consecutive values of row `row` at column `col`.
+template <int W, typename T>
+__device__ __forceinline__ void storew(T* __restrict__ M, int64_t n, int64_t row, int64_t col, const T* v, bool vec) {
   if (row >= n) return;
-  int32_t* p = M + row * n + col;
-  if (vec && col + 3 < n) {
-    *reinterpret_cast<int4*>(p) = v;
+  T* p = M + row * n + col;
+  if (W == 4 && vec && col + 3 < n) {
+    if constexpr (sizeof(T) == 4) {
+      using V4 = typename std::conditional<std::is_same<T, float>::value, float4, int4>::type;
+      V4 q;
+      q.x = v[0]; q.y = v[1]; q.z = v[2]; q.w = v[3];
+      *reinterpret_cast<V4*>(p) = q;
+    }
     return;
   }
-  if (col + 0 < n) p[0] = v.x;
-  if (col + 1 < n) p[1] = v.y;
-  if (col + 2 < n) p[2] = v.z;
-  if (col + 3 < n) p[3] = v.w;
+  if (W == 2 && vec && col + 1 < n) {
+    using V2 = typename std::conditional<std::is_same<T, float>::value, float2, int2>::type;
+    V2 q;
+    q.x = v[0]; q.y = v[1];
+    *reinterpret_cast<V2*>(p) = q;
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    if (col + k < n) p[k] = v[k];
 }
 
 // {acc0, acc1} += {[min(a0, b0) > t], [min(a1, b1) > t]} for two consecutive z.
@@ -119,78 +130,78 @@ __device__ __forceinline__ int count_of(uint64_t acc) {
   return static_cast<int>(lo) + static_cast<int>(hi);
 }
 
-// Computes and stores U[X, Y] (and U[Y, X] when bi != bj) for tile (bi, bj).
-// `smem` holds Geom::SMEM_FLOATS floats.  Must be called by all NT threads.
-template <int BM, int G>
+template <class Geo>
+struct FocusSmem {
+  static constexpr int FLOATS = 2 * (Geo::SX + Geo::SY);  // two stages of both operands
+};
+
+// Computes and stores U[X, Y] (and U[Y, X] off the diagonal) for super-tile
+// (bi, bj), column slice `slice`.  `smem` holds FocusSmem<Geo>::FLOATS
+// floats.  Must be called by all Geo::NT threads.
+template <class Geo>
 __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t n, int32_t* __restrict__ U, int bi,
-                                           int bj, float scale, float* smem) {
-  using Geo = FocusGeom<BM, G>;
-  constexpr int BK = Geo::BK, TM = Geo::TM, TPD = Geo::TPD, NT = Geo::NT;
-  const int64_t X0 = static_cast<int64_t>(bi) * BM, Y0 = static_cast<int64_t>(bj) * BM;
-  const int tx = threadIdx.x % TPD, ty = threadIdx.x / TPD;
+                                           int bj, int slice, float scale, float* smem) {
+  constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY, NT = Geo::NT;
+  const int64_t X0 = static_cast<int64_t>(bi) * Geo::B;
+  const int64_t Y0 = static_cast<int64_t>(bj) * Geo::B + static_cast<int64_t>(slice) * Geo::BY;
+  const int tx = threadIdx.x % Geo::TPX, ty = threadIdx.x / Geo::TPX;
   const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(D) % 16) == 0;
 
-  float* As = smem;                    // [2][BK][BM]  D[z][X0 + .]
-  float* Bs = smem + 2 * Geo::STAGE;   // [2][BK][BM]  D[z][Y0 + .]
+  float* As = smem;                   // [2][BK][BX]  D[z][X0 + .]
+  float* Bs = smem + 2 * Geo::SX;     // [2][BK][BY]  D[z][Y0 + .]
 
   const int64_t nstages = (n + BK - 1) / BK;
-  stage_rows<BM, NT, BK>(As, D, n, 0, X0, vec);
-  stage_rows<BM, NT, BK>(Bs, D, n, 0, Y0, vec);
+  stage_rows<Geo::BX, NT, BK>(As, D, n, 0, X0, vec);
+  stage_rows<Geo::BY, NT, BK>(Bs, D, n, 0, Y0, vec);
   cp_async_commit();
 
   // thresholds t = d_xy -> c = -t * scale (exact: power-of-two scaling)
-  float cst[TM][TM];
-  uint64_t acc[TM][TM];
+  float cst[TX][TY];
+  uint64_t acc[TX][TY];
 #pragma unroll
-  for (int gi = 0; gi < G; ++gi)
+  for (int i = 0; i < TX; ++i) {
+    const int64_t x = X0 + Geo::row_off(tx, i);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t x = X0 + gi * (BM / G) + 4 * tx + i;
-#pragma unroll
-      for (int gj = 0; gj < G; ++gj) {
-        const float4 t = load4(D, n, x, Y0 + gj * (BM / G) + 4 * ty, vec);
-        cst[gi * 4 + i][gj * 4 + 0] = -t.x * scale;
-        cst[gi * 4 + i][gj * 4 + 1] = -t.y * scale;
-        cst[gi * 4 + i][gj * 4 + 2] = -t.z * scale;
-        cst[gi * 4 + i][gj * 4 + 3] = -t.w * scale;
-      }
+    for (int j = 0; j < TY; ++j) {
+      const int64_t y = Y0 + Geo::col_off(ty, j);
+      cst[i][j] = (x < n && y < n) ? -__ldg(D + x * n + y) * scale : 0.f;
     }
+  }
 #pragma unroll
-  for (int i = 0; i < TM; ++i)
+  for (int i = 0; i < TX; ++i)
 #pragma unroll
-    for (int j = 0; j < TM; ++j) acc[i][j] = 0ull;
+    for (int j = 0; j < TY; ++j) acc[i][j] = 0ull;
 
   for (int64_t st = 0; st < nstages; ++st) {
     const int buf = static_cast<int>(st & 1);
     if (st + 1 < nstages) {
-      stage_rows<BM, NT, BK>(As + (buf ^ 1) * Geo::STAGE, D, n, (st + 1) * BK, X0, vec);
-      stage_rows<BM, NT, BK>(Bs + (buf ^ 1) * Geo::STAGE, D, n, (st + 1) * BK, Y0, vec);
+      stage_rows<Geo::BX, NT, BK>(As + (buf ^ 1) * Geo::SX, D, n, (st + 1) * BK, X0, vec);
+      stage_rows<Geo::BY, NT, BK>(Bs + (buf ^ 1) * Geo::SY, D, n, (st + 1) * BK, Y0, vec);
       cp_async_commit();
       cp_async_wait<1>();
     } else {
       cp_async_wait<0>();
     }
     __syncthreads();
-    const float* as = As + buf * Geo::STAGE;
-    const float* bs = Bs + buf * Geo::STAGE;
+    const float* as = As + buf * Geo::SX;
+    const float* bs = Bs + buf * Geo::SY;
 #pragma unroll
     for (int kk = 0; kk < BK; kk += 2) {
-      float a0[TM], b0[TM], a1[TM], b1[TM];
+      float a0[TX], b0[TY], a1[TX], b1[TY];
 #pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const float4 va0 = *reinterpret_cast<const float4*>(as + kk * BM + g * (BM / G) + 4 * tx);
-        const float4 vb0 = *reinterpret_cast<const float4*>(bs + kk * BM + g * (BM / G) + 4 * ty);
-        const float4 va1 = *reinterpret_cast<const float4*>(as + (kk + 1) * BM + g * (BM / G) + 4 * tx);
-        const float4 vb1 = *reinterpret_cast<const float4*>(bs + (kk + 1) * BM + g * (BM / G) + 4 * ty);
-        a0[4 * g + 0] = va0.x; a0[4 * g + 1] = va0.y; a0[4 * g + 2] = va0.z; a0[4 * g + 3] = va0.w;
-        b0[4 * g + 0] = vb0.x; b0[4 * g + 1] = vb0.y; b0[4 * g + 2] = vb0.z; b0[4 * g + 3] = vb0.w;
-        a1[4 * g + 0] = va1.x; a1[4 * g + 1] = va1.y; a1[4 * g + 2] = va1.z; a1[4 * g + 3] = va1.w;
-        b1[4 * g + 0] = vb1.x; b1[4 * g + 1] = vb1.y; b1[4 * g + 2] = vb1.z; b1[4 * g + 3] = vb1.w;
+      for (int g = 0; g < Geo::GX; ++g) {
+        lds<4>(as + kk * Geo::BX + Geo::row_off(tx, 4 * g), a0 + 4 * g);
+        lds<4>(as + (kk + 1) * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
       }
 #pragma unroll
-      for (int i = 0; i < TM; ++i)
+      for (int g = 0; g < Geo::GY; ++g) {
+        lds<Geo::CW>(bs + kk * Geo::BY + Geo::col_off(ty, Geo::CW * g), b0 + Geo::CW * g);
+        lds<Geo::CW>(bs + (kk + 1) * Geo::BY + Geo::col_off(ty, Geo::CW * g), b1 + Geo::CW * g);
+      }
 #pragma unroll
-        for (int j = 0; j < TM; ++j) focus_step2(acc[i][j], a0[i], b0[j], a1[i], b1[j], scale, cst[i][j]);
+      for (int i = 0; i < TX; ++i)
+#pragma unroll
+        for (int j = 0; j < TY; ++j) focus_step2(acc[i][j], a0[i], b0[j], a1[i], b1[j], scale, cst[i][j]);
     }
     __syncthreads();
   }
@@ -198,34 +209,28 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
   // u = n - #{z : min > t}; zero-filled z beyond n never count (m = 0 <= t)
   const int nn = static_cast<int>(n);
 #pragma unroll
-  for (int gi = 0; gi < G; ++gi)
+  for (int i = 0; i < TX; ++i) {
+    const int64_t x = X0 + Geo::row_off(tx, i);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int64_t x = X0 + gi * (BM / G) + 4 * tx + i;
-      const int r = gi * 4 + i;
+    for (int gj = 0; gj < Geo::GY; ++gj) {
+      int32_t v[Geo::CW];
 #pragma unroll
-      for (int gj = 0; gj < G; ++gj) {
-        const int c = gj * 4;
-        int4 v = make_int4(nn - count_of(acc[r][c + 0]), nn - count_of(acc[r][c + 1]),
-                           nn - count_of(acc[r][c + 2]), nn - count_of(acc[r][c + 3]));
-        store4i(U, n, x, Y0 + gj * (BM / G) + 4 * ty, v, vec);
-      }
+      for (int k = 0; k < Geo::CW; ++k) v[k] = nn - count_of(acc[i][Geo::CW * gj + k]);
+      storew<Geo::CW>(U, n, x, Y0 + Geo::col_off(ty, Geo::CW * gj), v, vec);
     }
+  }
   if (bi != bj) {
 #pragma unroll
-    for (int gj = 0; gj < G; ++gj)
+    for (int j = 0; j < TY; ++j) {
+      const int64_t y = Y0 + Geo::col_off(ty, j);
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t y = Y0 + gj * (BM / G) + 4 * ty + j;
-        const int c = gj * 4 + j;
+      for (int gi = 0; gi < Geo::GX; ++gi) {
+        int32_t v[4];
 #pragma unroll
-        for (int gi = 0; gi < G; ++gi) {
-          const int r = gi * 4;
-          int4 v = make_int4(nn - count_of(acc[r + 0][c]), nn - count_of(acc[r + 1][c]),
-                             nn - count_of(acc[r + 2][c]), nn - count_of(acc[r + 3][c]));
-          store4i(U, n, y, X0 + gi * (BM / G) + 4 * tx, v, vec);
-        }
+        for (int k = 0; k < 4; ++k) v[k] = nn - count_of(acc[4 * gi + k][j]);
+        storew<4>(U, n, y, X0 + Geo::row_off(tx, 4 * gi), v, vec);
       }
+    }
   }
 }
 

@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "pald_internal.cuh"
+#include "schedules.cuh"
 
 namespace pald {
 
@@ -20,7 +21,7 @@ bool opts_ok(const pald_opts* o) {
   if (!o) return true;
   if (o->reserved != 0) return false;
   if (o->accum_mode != PALD_ACCUM_COMPENSATED && o->accum_mode != PALD_ACCUM_PLAIN) return false;
-  if (o->schedule_id < -1 || o->schedule_id > 1) return false;
+  if (o->schedule_id < -1 || o->schedule_id >= kScheduleCount) return false;
   return true;
 }
 
@@ -156,12 +157,15 @@ pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_
   return PALD_OK;
 }
 
-int32_t pald_schedule_count(void) { return 2; }
+int32_t pald_schedule_count(void) { return kScheduleCount; }
 
 const char* pald_schedule_name(int32_t id) {
   switch (id) {
-    case 0: return "focus 64x64 tiles / cohesion 64x64 tiles (4x4 pairs per thread)";
-    case 1: return "focus 32x32 tiles / cohesion 32x32 tiles (4x4 pairs per thread)";
+    case 0: return "focus 64x64 tile, 4x4 pairs/thread, 16-deep stages | cohesion 64x64, 4x4, 16-deep";
+    case 1: return "focus 32x32 tile, 4x4 pairs/thread | cohesion 32x32, 4x4 (small matrices)";
+    case 2: return "focus 64x64 tile, 4x4, 32-deep stages | cohesion 64x32 slices, 4x2 pairs/thread, 16-deep";
+    case 3: return "focus 128x64 slices, 8x4 pairs/thread | cohesion 64x64, 4x4, 32-deep stages";
+    case 4: return "focus 64x32 slices, 4x4, 32-deep | cohesion 64x32 slices, 4x2, 32-deep";
     default: return nullptr;
   }
 }

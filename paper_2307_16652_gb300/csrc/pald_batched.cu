@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "cohesion_core.cuh"
+#include "schedules.cuh"
 
 namespace pald {
 
@@ -29,10 +30,10 @@ pald_opts opts_or_default(const pald_opts* o);
 
 namespace {
 
-constexpr int kBF = kBatchedFocusTile;     // 64
-constexpr int kBC = kBatchedCohesionTile;  // 64
-using FG = FocusGeom<kBF, 1>;
-using CG = CohesionGeom<kBC, 1>;
+using FG = FocusS0;     // 64 x 64 super-tiles, one CTA each
+using CG = CohesionS0;  // 64 x 64 super-tiles, one CTA each
+constexpr int kBF = FG::B;
+constexpr int kBC = CG::B;
 constexpr int kScanBlocksPerMatrix = 4;
 
 __global__ void __launch_bounds__(256) batched_scan_kernel(const float* __restrict__ D,
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(FG::NT, 2) batched_focus_kernel(const float* _
                                                                const ScanResult* __restrict__ scans,
                                                                const WorkItem* __restrict__ items, int64_t n_items,
                                                                int* counter) {
-  __shared__ __align__(16) float smem[FG::SMEM_FLOATS];
+  extern __shared__ __align__(16) float smem[];
   __shared__ int slot;
   for (;;) {
     const int64_t it = next_item(counter, &slot);
@@ -81,7 +82,7 @@ __global__ void __launch_bounds__(FG::NT, 2) batched_focus_kernel(const float* _
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
     const float scale = focus_scale(scans[w.matrix].inv_min_pos_bits);
-    focus_tile<kBF, 1>(D + md.off, md.n, U + md.off, w.bi, w.bj, scale, smem);
+    focus_tile<FG>(D + md.off, md.n, U + md.off, w.bi, w.bj, w.slice, scale, smem);
   }
 }
 
@@ -100,23 +101,22 @@ __global__ void __launch_bounds__(CG::NT) batched_cohesion_kernel(const float* _
                                                                   const MatrixDesc* __restrict__ mats,
                                                                   const WorkItem* __restrict__ items,
                                                                   int64_t n_items, int* counter) {
-  __shared__ __align__(16) float smem[CG::SMEM_FLOATS];
+  extern __shared__ __align__(16) float smem[];
   __shared__ int slot;
   for (;;) {
     const int64_t it = next_item(counter, &slot);
     if (it >= n_items) break;
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
-    cohesion_tile<kBC, 1, MODE>(D + md.off, R + md.off, md.n, C + md.off, w.bi, w.bj, smem);
+    cohesion_tile<CG, MODE>(D + md.off, R + md.off, md.n, C + md.off, w.bi, w.bj, w.slice, smem);
   }
 }
 
-int resident_ctas(const void* fn, int threads) {
-  int dev = 0, sms = 148, per = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, 0) != cudaSuccess || per < 1) per = 1;
-  return sms * per;
+int resident_ctas(const void* fn, int threads, int smem) {
+  int per = 1;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1) per = 1;
+  return sm_count() * per;
 }
 
 // ---------------------------------------------------------------------------
@@ -178,9 +178,11 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   for (int i : order) {
     const int Tf = static_cast<int>((ns[i] + kBF - 1) / kBF), Tc = static_cast<int>((ns[i] + kBC - 1) / kBC);
     for (int bi = 0; bi < Tf; ++bi)
-      for (int bj = bi; bj < Tf; ++bj) fitems.push_back(WorkItem{i, bi, bj, 0});
+      for (int bj = bi; bj < Tf; ++bj)
+        for (int h = 0; h < FG::H; ++h) fitems.push_back(WorkItem{i, bi, bj, h});
     for (int bi = 0; bi < Tc; ++bi)
-      for (int bj = bi; bj < Tc; ++bj) citems.push_back(WorkItem{i, bi, bj, 0});
+      for (int bj = bi; bj < Tc; ++bj)
+        for (int h = 0; h < CG::H; ++h) citems.push_back(WorkItem{i, bi, bj, h});
   }
   const size_t o_mats = 0;
   const size_t o_scans = align_up(o_mats + sizeof(MatrixDesc) * count, 256);
@@ -220,24 +222,30 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     g_capture_stream[device] = cs;
   }
   const bool plain = o.accum_mode == PALD_ACCUM_PLAIN;
-  const int gf = resident_ctas(reinterpret_cast<const void*>(batched_focus_kernel), FG::NT);
+  const int fsmem = FocusSmem<FG>::FLOATS * static_cast<int>(sizeof(float));
+  const int csmem = CohesionSmem<CG>::FLOATS * static_cast<int>(sizeof(float));
+  const int gf = resident_ctas(reinterpret_cast<const void*>(batched_focus_kernel), FG::NT, fsmem);
   const void* cfn = plain ? reinterpret_cast<const void*>(batched_cohesion_kernel<PALD_ACCUM_PLAIN>)
                           : reinterpret_cast<const void*>(batched_cohesion_kernel<PALD_ACCUM_COMPENSATED>);
-  const int gc = resident_ctas(cfn, CG::NT);
+  const int gc = resident_ctas(cfn, CG::NT, csmem);
+  if (gf == 0 || gc == 0) {
+    destroy_plan(p);
+    return cuda_fail(cudaErrorInvalidValue);
+  }
 
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     cudaMemsetAsync(d_scans, 0, sizeof(ScanResult) * count, cs);
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), cs);
     batched_scan_kernel<<<dim3(kScanBlocksPerMatrix, count), 256, 0, cs>>>(D, d_mats, d_scans);
-    batched_focus_kernel<<<gf, FG::NT, 0, cs>>>(D, U, d_mats, d_scans, d_fitems,
+    batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_mats, d_scans, d_fitems,
                                                 static_cast<int64_t>(fitems.size()), d_counters);
     batched_reciprocal_kernel<<<dim3(8, count), 256, 0, cs>>>(U, d_recip, d_mats);
     if (plain)
-      batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, 0, cs>>>(
+      batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, csmem, cs>>>(
           D, d_recip, C, d_mats, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
     else
-      batched_cohesion_kernel<PALD_ACCUM_COMPENSATED><<<gc, CG::NT, 0, cs>>>(
+      batched_cohesion_kernel<PALD_ACCUM_COMPENSATED><<<gc, CG::NT, csmem, cs>>>(
           D, d_recip, C, d_mats, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
     cudaError_t launch_err = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &p.graph);

@@ -116,12 +116,7 @@ struct MatrixDesc {
 struct WorkItem {
   int32_t matrix;
   int32_t bi, bj;
-  int32_t pad;
+  int32_t slice;  // column slice of the super-tile
 };
-
-// Tile edge of each pass (elements).
-constexpr int kCohesionTile = 64;
-constexpr int kBatchedFocusTile = 64;
-constexpr int kBatchedCohesionTile = 64;
 
 }  // namespace pald
