@@ -27,7 +27,9 @@
  *     default stream), except that validation copies one small status word to
  *     the host and synchronises `stream`.
  *   - Scratch memory that a call needs is taken with cudaMallocAsync on
- *     `stream` and released on the same stream before the call returns.
+ *     `stream` and released on the same stream before the call returns
+ *     (pald_cohesion_noalloc and pald_batched's cached plans are the
+ *     exceptions, described with them).
  *   - Every function returns a status and never aborts, traps or prints.
  *     On any error the contents of the outputs are unspecified.
  */
@@ -58,11 +60,12 @@ typedef enum pald_status {
 
 /* Accumulation of the cohesion sums (pass 2). */
 enum {
-  /* FP32 partial sums over 16 consecutive y, folded into an FP32 running sum
-   * with an error-free TwoSum whose error is carried into the next partial;
-   * FP64 final merge, 1/(n-1) in FP64, one rounding to FP32 (default). */
+  /* FP32 partial sums over 4 consecutive y, folded into an FP32 running sum
+   * (biased so that Fast2Sum is error-free) whose exact error is carried into
+   * the next partial; FP64 final merge, 1/(n-1) in FP64, one rounding to FP32
+   * (default). */
   PALD_ACCUM_COMPENSATED = 0,
-  /* one FP32 running sum per entry, normalised in FP32 (precision baseline) */
+  /* one FP32 running sum per entry (precision baseline), normalised in FP64 */
   PALD_ACCUM_PLAIN = 1
 };
 
@@ -131,6 +134,27 @@ pald_status pald_batched(int32_t count, const int64_t* n_host, const int64_t* of
  */
 pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_host,
                       const pald_opts* opts);
+
+/*
+ * pald_cohesion_noalloc - pass 2 for callers that must not allocate device
+ * memory.  (The paper has no counterpart: this is a deployment variant.)
+ * It computes exactly what pald_cohesion computes, with the same kernels,
+ * but it never calls cudaMalloc, cudaMallocAsync, cudaFree or any other
+ * allocating routine.  Its scratch (R = 1/u) is a fixed array built into the
+ * library, 16 MiB + 256 bytes, which every GPU that loads the library holds
+ * until the process exits.
+ *   D, U, n, C, opts, stream  as pald_cohesion, with 2 <= n <= 2048.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture
+ * begins.  Every call on a device shares the one array and overwrites it:
+ * calls whose GPU work overlaps in time (different streams, or different host
+ * threads on the same device) race on it and must be serialised by the
+ * caller, for example by issuing them on one stream.
+ * Errors: UNSUPPORTED for n > 2048 (the array is too small); otherwise as
+ * pald_cohesion.
+ */
+pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, int64_t n, float* C,
+                                  const pald_opts* opts, pald_stream_t stream);
 
 /*
  * pald_validate - check the input contract of D (see above) on the device.

@@ -22,6 +22,7 @@ from .binding import (  # noqa: F401
     library_path,
     pald_batched,
     pald_cohesion,
+    pald_cohesion_noalloc,
     pald_focus,
     pald_host,
     pald_release,
@@ -34,6 +35,6 @@ from .binding import (  # noqa: F401
 
 __all__ = [
     "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PaldError", "lib", "library_path",
-    "pald_batched", "pald_cohesion", "pald_focus", "pald_host", "pald_release",
+    "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_release",
     "pald_schedule_count", "pald_schedule_name", "pald_status_string", "pald_validate", "pald_version",
 ]

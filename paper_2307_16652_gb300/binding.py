@@ -61,10 +61,12 @@ def _lib() -> ctypes.CDLL:
         op = ctypes.POINTER(PaldOpts)
         h.pald_focus.argtypes = [vp, i64, vp, op, vp]
         h.pald_cohesion.argtypes = [vp, vp, i64, vp, op, vp]
+        h.pald_cohesion_noalloc.argtypes = [vp, vp, i64, vp, op, vp]
         h.pald_batched.argtypes = [i32, vp, vp, vp, vp, vp, op, vp]
         h.pald_host.argtypes = [vp, i64, vp, vp, op]
         h.pald_validate.argtypes = [vp, i64, vp]
-        for f in (h.pald_focus, h.pald_cohesion, h.pald_batched, h.pald_host, h.pald_validate):
+        for f in (h.pald_focus, h.pald_cohesion, h.pald_cohesion_noalloc, h.pald_batched, h.pald_host,
+                  h.pald_validate):
             f.restype = ctypes.c_int
         h.pald_status_string.argtypes = [ctypes.c_int]
         h.pald_status_string.restype = ctypes.c_char_p
@@ -139,6 +141,23 @@ def pald_cohesion(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED,
     st = _lib().pald_cohesion(_check(D, torch.float32, n, "D"), _check(U, torch.int32, n, "U"), n,
                               _check(C, torch.float32, n, "C"), ctypes.byref(o), _stream_ptr(stream))
     _raise(st, "pald_cohesion")
+    return C
+
+
+def pald_cohesion_noalloc(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1,
+                          stream=None):
+    """Pass 2 for callers that must not allocate device memory (n <= 2048).
+
+    Same result as :func:`pald_cohesion`; the scratch is a fixed array inside
+    the library, shared by every call on a device, so calls must not overlap
+    on the GPU."""
+    import torch
+
+    n = D.shape[0]
+    o = _opts(validate, accum_mode, schedule_id)
+    st = _lib().pald_cohesion_noalloc(_check(D, torch.float32, n, "D"), _check(U, torch.int32, n, "U"), n,
+                                      _check(C, torch.float32, n, "C"), ctypes.byref(o), _stream_ptr(stream))
+    _raise(st, "pald_cohesion_noalloc")
     return C
 
 
