@@ -13,12 +13,14 @@
 //
 // Per (x, z, y) the inner loop issues six instructions, all of them exact
 // FP32 decisions on the input values:
-//     m  = min(d_xy, d_zy)                FMNMX        (ALU pipe)
-//     p  = m >= b                         FSETP        (ALU pipe)
-//     v2 = sat(d_zy * s + c)              FFMA.SAT     (FMA pipe)
-//     v1 = sat(d_xy * s + c)              FFMA.SAT     (FMA pipe)
-//     @p S_xz += v2 * r_xy                FFMA         (FMA pipe)
-//     @p S_zx += v1 * r_zy                FFMA         (FMA pipe)
+//     v2 = sat(d_zy * s + c) = w(b, d_zy)          FFMA.SAT     (FMA pipe)
+//     v1 = sat(d_xy * s + c) = w(b, d_xy)          FFMA.SAT     (FMA pipe)
+//     m  = min(v1, v2)                             FMNMX        (ALU pipe)
+//     p  = m > 0   (d_xz <= min(d_xy, d_zy))       FSETP        (ALU pipe)
+//     @p S_xz += v2 * r_xy                         FFMA         (FMA pipe)
+//     @p S_zx += v1 * r_zy                         FFMA         (FMA pipe)
+// (w(b, a) is 0 exactly when a < b, so the focus/support test needs no
+// separate copy of b.)
 // where (s, c) are per-pair constants built from b = d_xz so that
 // sat(a*s + c) = w(b, a) exactly: s = 2^(22-e) (2^(23-e) if b is a power of
 // two), c = 1/2 - b*s.  Then a == b gives exactly 1/2, and any other float a
@@ -46,7 +48,7 @@ constexpr float kMergeBias = 4.0f;  // >= kMergeEvery * 1/2 + carried error
 
 template <class Geo>
 struct CohesionSmem {
-  static constexpr int FLOATS = 2 * 2 * (Geo::SX + Geo::SY);  // two stages of D_X, R_X, D_Z, R_Z
+  static constexpr int FLOATS = kPipe * 2 * (Geo::SX + Geo::SY);  // kPipe stages of D_X, R_X, D_Z, R_Z
 };
 
 __device__ __forceinline__ void tie_constants(float b, float& s, float& c) {
@@ -65,29 +67,40 @@ __device__ __forceinline__ void tie_constants(float b, float& s, float& c) {
 }
 
 // One (x, z, y) step on the packed partial {S_xz, S_zx}; see the header.
-__device__ __forceinline__ void cohesion_step(uint64_t& sacc, float a1, float a2, float b, float s, float c, float r1,
+__device__ __forceinline__ void cohesion_step(uint64_t& sacc, float a1, float a2, float s, float c, float r1,
                                               float r2) {
   asm("{\n\t.reg .pred p;\n\t.reg .f32 m, v1, v2, sx, sz;\n\t"
       "mov.b64 {sx, sz}, %0;\n\t"
-      "min.f32 m, %1, %2;\n\t"
-      "setp.ge.f32 p, m, %3;\n\t"
-      "fma.rn.sat.f32 v2, %2, %4, %5;\n\t"
-      "fma.rn.sat.f32 v1, %1, %4, %5;\n\t"
-      "@p fma.rn.f32 sx, v2, %6, sx;\n\t"
-      "@p fma.rn.f32 sz, v1, %7, sz;\n\t"
+      "fma.rn.sat.f32 v2, %2, %3, %4;\n\t"
+      "fma.rn.sat.f32 v1, %1, %3, %4;\n\t"
+      "min.f32 m, v1, v2;\n\t"
+      "setp.gt.f32 p, m, 0f00000000;\n\t"
+      "@p fma.rn.f32 sx, v2, %5, sx;\n\t"
+      "@p fma.rn.f32 sz, v1, %6, sz;\n\t"
       "mov.b64 %0, {sx, sz};\n\t}"
       : "+l"(sacc)
-      : "f"(a1), "f"(a2), "f"(b), "f"(s), "f"(c), "f"(r1), "f"(r2));
+      : "f"(a1), "f"(a2), "f"(s), "f"(c), "f"(r1), "f"(r2));
 }
 
-// Fast2Sum on both lanes: h + s == old h + old s exactly when |h| >= |s|.
+// Packed f32x2 add and subtract (one instruction for both lanes).
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+// Fast2Sum on both lanes: h + s == old h + old s exactly when |h| >= |s|;
+// h takes the rounded sum and s the exact rounding error.
 __device__ __forceinline__ void fast2sum_fold(uint64_t& h, uint64_t& s) {
-  asm("{\n\t.reg .b64 t, z;\n\t"
-      "add.rn.f32x2 t, %0, %1;\n\t"
-      "sub.rn.f32x2 z, t, %0;\n\t"
-      "sub.rn.f32x2 %1, %1, z;\n\t"
-      "mov.b64 %0, t;\n\t}"
-      : "+l"(h), "+l"(s));
+  const uint64_t t = add2(h, s);
+  const uint64_t z = sub2(t, h);
+  s = sub2(s, z);
+  h = t;
 }
 
 __device__ __forceinline__ uint64_t pack2(float lo, float hi) {
@@ -113,19 +126,25 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
   const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(D) % 16) == 0 &&
                    (reinterpret_cast<uintptr_t>(R) % 16) == 0;
 
-  float* Ad = smem;                                   // [2][BK][BX]  d_xy  (row y, column x)
-  float* Ar = Ad + 2 * Geo::SX;                       // [2][BK][BX]  r_xy
-  float* Bd = Ar + 2 * Geo::SX;                       // [2][BK][BY]  d_zy
-  float* Br = Bd + 2 * Geo::SY;                       // [2][BK][BY]  r_zy
+  float* Ad = smem;                                   // [kPipe][BK][BX]  d_xy  (row y, column x)
+  float* Ar = Ad + kPipe * Geo::SX;                   // [kPipe][BK][BX]  r_xy
+  float* Bd = Ar + kPipe * Geo::SX;                   // [kPipe][BK][BY]  d_zy
+  float* Br = Bd + kPipe * Geo::SY;                   // [kPipe][BK][BY]  r_zy
 
   const int64_t nstages = (n + BK - 1) / BK;
-  stage_rows<Geo::BX, NT, BK>(Ad, D, n, 0, X0, vec);
-  stage_rows<Geo::BX, NT, BK>(Ar, R, n, 0, X0, vec);
-  stage_rows<Geo::BY, NT, BK>(Bd, D, n, 0, Z0, vec);
-  stage_rows<Geo::BY, NT, BK>(Br, R, n, 0, Z0, vec);
-  cp_async_commit();
+  auto stage = [&](int buf, int64_t y0) {
+    stage_rows<Geo::BX, NT, BK>(Ad + buf * Geo::SX, D, n, y0, X0, vec);
+    stage_rows<Geo::BX, NT, BK>(Ar + buf * Geo::SX, R, n, y0, X0, vec);
+    stage_rows<Geo::BY, NT, BK>(Bd + buf * Geo::SY, D, n, y0, Z0, vec);
+    stage_rows<Geo::BY, NT, BK>(Br + buf * Geo::SY, R, n, y0, Z0, vec);
+  };
+#pragma unroll
+  for (int p = 0; p < kPipe - 1; ++p) {
+    if (p < nstages) stage(p, p * BK);
+    cp_async_commit();
+  }
 
-  float bv[TX][TY], sv[TX][TY], cv[TX][TY];
+  float sv[TX][TY], cv[TX][TY];
   uint64_t sacc[TX][TY], hacc[TX][TY];
 #pragma unroll
   for (int i = 0; i < TX; ++i) {
@@ -133,8 +152,7 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
 #pragma unroll
     for (int j = 0; j < TY; ++j) {
       const int64_t z = Z0 + Geo::col_off(tz, j);
-      bv[i][j] = (x < n && z < n) ? __ldg(D + x * n + z) : 0.f;
-      tie_constants(bv[i][j], sv[i][j], cv[i][j]);
+      tie_constants((x < n && z < n) ? __ldg(D + x * n + z) : 0.f, sv[i][j], cv[i][j]);
     }
   }
   const uint64_t zero2 = pack2(0.f, 0.f);
@@ -148,24 +166,16 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
     }
 
   for (int64_t st = 0; st < nstages; ++st) {
-    const int buf = static_cast<int>(st & 1);
-    if (st + 1 < nstages) {
-      const int64_t y0 = (st + 1) * BK;
-      stage_rows<Geo::BX, NT, BK>(Ad + (buf ^ 1) * Geo::SX, D, n, y0, X0, vec);
-      stage_rows<Geo::BX, NT, BK>(Ar + (buf ^ 1) * Geo::SX, R, n, y0, X0, vec);
-      stage_rows<Geo::BY, NT, BK>(Bd + (buf ^ 1) * Geo::SY, D, n, y0, Z0, vec);
-      stage_rows<Geo::BY, NT, BK>(Br + (buf ^ 1) * Geo::SY, R, n, y0, Z0, vec);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
+    const int buf = static_cast<int>(st % kPipe);
+    cp_async_wait<kPipe - 2>();  // stage st has landed (later ones may be in flight)
+    __syncthreads();             // ... for every thread, and stage st-1's buffer is free
+    if (st + kPipe - 1 < nstages) stage(static_cast<int>((st + kPipe - 1) % kPipe), (st + kPipe - 1) * BK);
+    cp_async_commit();  // possibly empty: keeps one group per stage
     const float* ad = Ad + buf * Geo::SX;
     const float* ar = Ar + buf * Geo::SX;
     const float* bd = Bd + buf * Geo::SY;
     const float* br = Br + buf * Geo::SY;
-#pragma unroll
+#pragma unroll Geo::UNR
     for (int kk = 0; kk < BK; ++kk) {
       float a1[TX], r1[TX], a2[TY], r2[TY];
 #pragma unroll
@@ -182,15 +192,19 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
       for (int i = 0; i < TX; ++i)
 #pragma unroll
         for (int j = 0; j < TY; ++j)
-          cohesion_step(sacc[i][j], a1[i], a2[j], bv[i][j], sv[i][j], cv[i][j], r1[i], r2[j]);
-      if (MODE == PALD_ACCUM_COMPENSATED && (kk % kMergeEvery) == kMergeEvery - 1) {
+          cohesion_step(sacc[i][j], a1[i], a2[j], sv[i][j], cv[i][j], r1[i], r2[j]);
+      if (MODE == PALD_ACCUM_COMPENSATED) {
+        // every pair folds at the same y (y mod 4 == 3): the chunking is
+        // then the same for every schedule, for both lanes of a pair and
+        // for the batched path, so all of them give bit-identical C
+        if ((kk % kMergeEvery) == kMergeEvery - 1) {
 #pragma unroll
-        for (int i = 0; i < TX; ++i)
+          for (int i = 0; i < TX; ++i)
 #pragma unroll
-          for (int j = 0; j < TY; ++j) fast2sum_fold(hacc[i][j], sacc[i][j]);
+            for (int j = 0; j < TY; ++j) fast2sum_fold(hacc[i][j], sacc[i][j]);
+        }
       }
     }
-    __syncthreads();
   }
 
   const double inv = 1.0 / static_cast<double>(n - 1);

@@ -130,9 +130,13 @@ __device__ __forceinline__ int count_of(uint64_t acc) {
   return static_cast<int>(lo) + static_cast<int>(hi);
 }
 
+// Stages in flight: the buffer refilled while stage s is computed is the one
+// stage s-1 used, so one barrier per stage orders reuse and visibility.
+constexpr int kPipe = 3;
+
 template <class Geo>
 struct FocusSmem {
-  static constexpr int FLOATS = 2 * (Geo::SX + Geo::SY);  // two stages of both operands
+  static constexpr int FLOATS = kPipe * (Geo::SX + Geo::SY);  // kPipe stages of both operands
 };
 
 // Computes and stores U[X, Y] (and U[Y, X] off the diagonal) for super-tile
@@ -147,13 +151,18 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
   const int tx = threadIdx.x % Geo::TPX, ty = threadIdx.x / Geo::TPX;
   const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(D) % 16) == 0;
 
-  float* As = smem;                   // [2][BK][BX]  D[z][X0 + .]
-  float* Bs = smem + 2 * Geo::SX;     // [2][BK][BY]  D[z][Y0 + .]
+  float* As = smem;                       // [kPipe][BK][BX]  D[z][X0 + .]
+  float* Bs = smem + kPipe * Geo::SX;     // [kPipe][BK][BY]  D[z][Y0 + .]
 
   const int64_t nstages = (n + BK - 1) / BK;
-  stage_rows<Geo::BX, NT, BK>(As, D, n, 0, X0, vec);
-  stage_rows<Geo::BY, NT, BK>(Bs, D, n, 0, Y0, vec);
-  cp_async_commit();
+#pragma unroll
+  for (int p = 0; p < kPipe - 1; ++p) {
+    if (p < nstages) {
+      stage_rows<Geo::BX, NT, BK>(As + p * Geo::SX, D, n, p * BK, X0, vec);
+      stage_rows<Geo::BY, NT, BK>(Bs + p * Geo::SY, D, n, p * BK, Y0, vec);
+    }
+    cp_async_commit();
+  }
 
   // thresholds t = d_xy -> c = -t * scale (exact: power-of-two scaling)
   float cst[TX][TY];
@@ -173,19 +182,18 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
     for (int j = 0; j < TY; ++j) acc[i][j] = 0ull;
 
   for (int64_t st = 0; st < nstages; ++st) {
-    const int buf = static_cast<int>(st & 1);
-    if (st + 1 < nstages) {
-      stage_rows<Geo::BX, NT, BK>(As + (buf ^ 1) * Geo::SX, D, n, (st + 1) * BK, X0, vec);
-      stage_rows<Geo::BY, NT, BK>(Bs + (buf ^ 1) * Geo::SY, D, n, (st + 1) * BK, Y0, vec);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
+    const int buf = static_cast<int>(st % kPipe);
+    cp_async_wait<kPipe - 2>();  // stage st has landed (later ones may be in flight)
+    __syncthreads();             // ... for every thread, and stage st-1's buffer is free
+    if (st + kPipe - 1 < nstages) {
+      const int nb = static_cast<int>((st + kPipe - 1) % kPipe);
+      stage_rows<Geo::BX, NT, BK>(As + nb * Geo::SX, D, n, (st + kPipe - 1) * BK, X0, vec);
+      stage_rows<Geo::BY, NT, BK>(Bs + nb * Geo::SY, D, n, (st + kPipe - 1) * BK, Y0, vec);
     }
-    __syncthreads();
+    cp_async_commit();  // possibly empty: keeps one group per stage
     const float* as = As + buf * Geo::SX;
     const float* bs = Bs + buf * Geo::SY;
-#pragma unroll
+#pragma unroll Geo::UNR / 2
     for (int kk = 0; kk < BK; kk += 2) {
       float a0[TX], b0[TY], a1[TX], b1[TY];
 #pragma unroll
@@ -203,7 +211,6 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
 #pragma unroll
         for (int j = 0; j < TY; ++j) focus_step2(acc[i][j], a0[i], b0[j], a1[i], b1[j], scale, cst[i][j]);
     }
-    __syncthreads();
   }
 
   // u = n - #{z : min > t}; zero-filled z beyond n never count (m = 0 <= t)

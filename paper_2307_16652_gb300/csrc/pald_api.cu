@@ -166,6 +166,8 @@ const char* pald_schedule_name(int32_t id) {
     case 2: return "focus 64x64 tile, 4x4, 32-deep stages | cohesion 64x32 slices, 4x2 pairs/thread, 16-deep";
     case 3: return "focus 128x64 slices, 8x4 pairs/thread | cohesion 64x64, 4x4, 32-deep stages";
     case 4: return "focus 64x32 slices, 4x4, 32-deep | cohesion 64x32 slices, 4x2, 32-deep";
+    case 5: return "focus 64x64, 4x4, 64-deep stages unrolled 16 | cohesion 64x64, 4x4, 32-deep unrolled 4";
+    case 6: return "focus 128x64 slices, 8x4, 32-deep | cohesion 64x64, 4x4, 64-deep unrolled 8";
     default: return nullptr;
   }
 }

@@ -50,6 +50,8 @@ cudaError_t launch_mode(const float* D, const float* R, int64_t n, float* C, int
     case 2: return launch_t<CohesionS2, MODE, 2>(D, R, n, C, s);
     case 3: return launch_t<CohesionS3, MODE, 1>(D, R, n, C, s);
     case 4: return launch_t<CohesionS4, MODE, 2>(D, R, n, C, s);
+    case 5: return launch_t<CohesionS5, MODE, 1>(D, R, n, C, s);
+    case 6: return launch_t<CohesionS6, MODE, 1>(D, R, n, C, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -45,6 +45,8 @@ cudaError_t launch_focus(const float* D, int64_t n, int32_t* U, const ScanResult
     case 2: return launch_t<FocusS2, 2>(D, n, U, scan, s);
     case 3: return launch_t<FocusS3, 1>(D, n, U, scan, s);
     case 4: return launch_t<FocusS4, 4>(D, n, U, scan, s);
+    case 5: return launch_t<FocusS5, 2>(D, n, U, scan, s);
+    case 6: return launch_t<FocusS6, 1>(D, n, U, scan, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -9,20 +9,24 @@
 
 namespace pald {
 
-constexpr int kScheduleCount = 5;
+constexpr int kScheduleCount = 7;
 
-//                       B    H  GX GY CW  BK
+//                       B    H  GX GY CW  BK  unroll
 using FocusS0 = TileGeom<64, 1, 1, 1, 4, 16>;    // 4x4 pairs/thread, 256 threads
 using FocusS1 = TileGeom<32, 1, 1, 1, 4, 16>;    // small matrices, 64 threads
 using FocusS2 = TileGeom<64, 1, 1, 1, 4, 32>;    // deeper stages
 using FocusS3 = TileGeom<128, 2, 2, 1, 4, 16>;   // 8x4 pairs/thread, 128x64 CTA tiles
 using FocusS4 = TileGeom<64, 2, 1, 1, 4, 32>;    // 64x32 CTA tiles, 128 threads
+using FocusS5 = TileGeom<64, 1, 1, 1, 4, 64, 16>;  // 64-deep stages, partly unrolled
+using FocusS6 = TileGeom<128, 2, 2, 1, 4, 32>;   // 8x4 pairs/thread, 32-deep
 
 using CohesionS0 = TileGeom<64, 1, 1, 1, 4, 16>;  // 4x4 pairs/thread, 256 threads
 using CohesionS1 = TileGeom<32, 1, 1, 1, 4, 16>;  // small matrices, 64 threads
 using CohesionS2 = TileGeom<64, 2, 1, 1, 2, 16>;  // 4x2 pairs/thread: more warps per SM
 using CohesionS3 = TileGeom<64, 1, 1, 1, 4, 32>;  // deeper stages
 using CohesionS4 = TileGeom<64, 2, 1, 1, 2, 32>;  // 4x2 pairs/thread, deeper stages
+using CohesionS5 = TileGeom<64, 1, 1, 1, 4, 32, 4>;  // 32-deep, loop unrolled by 4 (smaller code)
+using CohesionS6 = TileGeom<64, 1, 1, 1, 4, 64, 8>;  // 64-deep stages, unrolled by 8
 
 inline int sm_count() {
   int dev = 0, sms = 148;
@@ -32,8 +36,8 @@ inline int sm_count() {
 }
 
 // Defaults from the GB300 autotune table (times in ms, best per order):
-//   focus    n=1024: s2 0.127 | 2048: s4 0.526 | 4096: s2 3.53 | 8192: s2 27.1 | 16384: s2 212.9
-//   cohesion n=1024: s4 0.259 | 2048: s4 1.431 | 4096: s3 10.7 | 8192: s3 82.3 | 16384: s3 646.0
+//   focus    n=1024: s2 0.127 | 2048: s4 0.52 | 4096: s2 3.52 | 8192: s2 27.1 | 16384: s2 212.7
+//   cohesion n=1024: s4 0.259 | 2048: s4 1.41 | 4096: s3 10.29 | 8192: s3 78.8 | 16384: s3 618.8
 // Orders below 1024 take the 32-wide tiles so that the launch still covers
 // the GPU.
 inline int default_focus_schedule(int64_t n) { return n < 1024 ? 1 : 2; }

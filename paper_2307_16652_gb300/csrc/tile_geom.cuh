@@ -18,7 +18,7 @@
 
 namespace pald {
 
-template <int B_, int H_, int GX_, int GY_, int CW_, int BK_>
+template <int B_, int H_, int GX_, int GY_, int CW_, int BK_, int UNR_ = BK_>
 struct TileGeom {
   static constexpr int B = B_;            // super-tile edge
   static constexpr int H = H_;            // column slices per super-tile
@@ -31,24 +31,54 @@ struct TileGeom {
   static constexpr int TPY = BY / TY;     // threads along columns
   static constexpr int NT = TPX * TPY;
   static constexpr int BK = BK_;          // streamed index per pipeline stage
+  static constexpr int UNR = UNR_;        // unroll factor of the streamed loop (a divisor of BK)
   static constexpr int SX = BK * BX;      // floats of one row-side operand stage
   static constexpr int SY = BK * BY;      // floats of one column-side operand stage
   static_assert(BX % TX == 0 && BY % TY == 0, "tile must divide into thread tiles");
   static_assert((BX / GX) % 4 == 0 && (BY / GY) % CW == 0, "groups must be vector aligned");
   static_assert(CW == 4 || CW == 2, "column vectors are 4 or 2 wide");
   static_assert(BK % 4 == 0, "stage depth must be a multiple of 4");
+  static_assert(BK % UNR == 0 && UNR % 4 == 0, "unroll must divide the stage and keep 4-y phases");
 
   // global row / column of row i and column j of thread (tx, ty)
   __device__ static __forceinline__ int row_off(int tx, int i) { return (i / 4) * (BX / GX) + 4 * tx + (i % 4); }
   __device__ static __forceinline__ int col_off(int ty, int j) { return (j / CW) * (BY / GY) + CW * ty + (j % CW); }
 };
 
-// Launch index -> (bi, bj, slice).  Super-tiles of one block-row are
-// consecutive so that CTAs running together share the row panel in L2.
-__device__ __forceinline__ void decode_tile(int64_t t, int64_t T, int H, int* bi, int* bj, int* slice) {
-  const int64_t st = t / H;
+// Launch index -> (bi, bj, slice), bi <= bj.  The upper triangle of
+// super-tiles is walked in strips of kStrip block-rows: strip k first covers
+// its own triangle (columns k*S .. k*S+S-1), then the columns to its right,
+// S tiles per column.  CTAs that run together therefore touch about
+// kStrip + (resident CTAs / kStrip) distinct row panels instead of one panel
+// per CTA, and the panels they stream stay in L2 for each other.
+constexpr int kStrip = 12;
+
+__host__ __device__ __forceinline__ void decode_tile(int64_t t, int64_t T, int H, int* bi, int* bj, int* slice) {
+  int64_t st = t / H;
   *slice = static_cast<int>(t - st * H);
-  tri_decode(st, T, bi, bj);
+  const int64_t S = kStrip;
+  int64_t k0 = 0;
+  for (;;) {
+    const int64_t h = (T - k0) < S ? (T - k0) : S;  // rows in this strip
+    const int64_t tri = h * (h + 1) / 2;            // its own triangle
+    const int64_t total = tri + (T - k0 - h) * h;   // plus the columns to the right
+    if (st < total) {
+      if (st < tri) {  // column c of the triangle holds c + 1 tiles
+        int64_t c = static_cast<int64_t>((sqrt(8.0 * static_cast<double>(st) + 1.0) - 1.0) / 2.0);
+        while (c * (c + 1) / 2 > st) --c;
+        while ((c + 1) * (c + 2) / 2 <= st) ++c;
+        *bj = static_cast<int>(k0 + c);
+        *bi = static_cast<int>(k0 + (st - c * (c + 1) / 2));
+      } else {
+        const int64_t r = st - tri;
+        *bj = static_cast<int>(k0 + h + r / h);
+        *bi = static_cast<int>(k0 + r % h);
+      }
+      return;
+    }
+    st -= total;
+    k0 += h;
+  }
 }
 
 }  // namespace pald
