@@ -54,7 +54,7 @@ typedef enum pald_status {
   PALD_ERR_BAD_VALUE = 4,      /* validation: NaN, inf, negative, -0.0, or out of range */
   PALD_ERR_CUDA = 5,           /* a CUDA runtime call failed (see pald_last_cuda_error) */
   PALD_ERR_NO_MEMORY = 6,      /* scratch allocation failed */
-  PALD_ERR_TIMEOUT = 7,        /* reserved: a bounded device-side wait gave up */
+  PALD_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up (pald_check_faults) */
   PALD_ERR_UNSUPPORTED = 8     /* size beyond what this build handles */
 } pald_status;
 
@@ -163,6 +163,38 @@ pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, int64_t n, f
  * found in the order NOT_SYMMETRIC, BAD_DIAGONAL, BAD_VALUE.
  */
 pald_status pald_validate(const float* D, int64_t n, pald_stream_t stream);
+
+/*
+ * pald_tie_map - diagnostic: the tie map that pald_cohesion builds for D and
+ * reads to pick, per tile and stage of 32 y, between its short inner loop
+ * (valid when no one-sided tie d_xy == d_xz or d_zy == d_zx can occur) and
+ * its long one.  The paper has no counterpart; both loops compute Sec. 2
+ * eq. (fxz) with the Sec. 5 tie split and give identical bits.
+ *   D    device, n x n FP32 (the input contract above).
+ *   map  device uint32 array of pald_tie_map_words(n) words, overwritten.
+ *        With nb = ceil(n/64) and wpp = ceil(ceil(n/32)/32): word
+ *        (a*nb + b)*wpp + g/32, a <= b, holds bit g%32 set when some row r
+ *        in block a or b (rows 64a.., 64b..) has equal entries at two
+ *        columns p != q with q in the other block of the pair and p in
+ *        y group g (columns 32g..32g+31); words nb*nb*wpp + a (a < nb) are
+ *        nonzero when a row of block a had too many repeated values to list
+ *        (the tile then runs the long loop throughout).
+ * Errors: INVALID_ARG (null pointer, n out of range); CUDA.
+ */
+pald_status pald_tie_map(const float* D, int64_t n, uint32_t* map, pald_stream_t stream);
+
+/* Words of the tie map for order n (0 if n is out of range). */
+int64_t pald_tie_map_words(int64_t n);
+
+/*
+ * pald_check_faults - synchronises `stream`, then reports whether a kernel of
+ * this library gave up a bounded device-side wait (a TMA copy that never
+ * completed within 2 s) since the previous call on this device, and clears
+ * that record.  Such a kernel stops early instead of hanging the GPU; the
+ * outputs of the call it belonged to are then unspecified.
+ * Returns PALD_OK, PALD_ERR_TIMEOUT, or PALD_ERR_CUDA.
+ */
+pald_status pald_check_faults(pald_stream_t stream);
 
 /* Number of built-in tile schedules and the name of schedule `id` (static
  * string, or NULL if id is out of range).  Used by the autotuner. */

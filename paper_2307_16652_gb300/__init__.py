@@ -19,6 +19,7 @@ from .binding import (  # noqa: F401
     PALD_ACCUM_PLAIN,
     PaldError,
     lib,
+    pald_check_faults,
     library_path,
     pald_batched,
     pald_cohesion,
@@ -29,12 +30,15 @@ from .binding import (  # noqa: F401
     pald_schedule_count,
     pald_schedule_name,
     pald_status_string,
+    pald_tie_map,
+    pald_tie_map_words,
     pald_validate,
     pald_version,
 )
 
 __all__ = [
-    "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PaldError", "lib", "library_path",
+    "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PaldError", "lib", "library_path", "pald_check_faults",
     "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_release",
-    "pald_schedule_count", "pald_schedule_name", "pald_status_string", "pald_validate", "pald_version",
+    "pald_schedule_count", "pald_schedule_name", "pald_status_string", "pald_tie_map", "pald_tie_map_words",
+    "pald_validate", "pald_version",
 ]

@@ -65,8 +65,12 @@ def _lib() -> ctypes.CDLL:
         h.pald_batched.argtypes = [i32, vp, vp, vp, vp, vp, op, vp]
         h.pald_host.argtypes = [vp, i64, vp, vp, op]
         h.pald_validate.argtypes = [vp, i64, vp]
+        h.pald_tie_map.argtypes = [vp, i64, vp, vp]
+        h.pald_check_faults.argtypes = [vp]
+        h.pald_tie_map_words.argtypes = [i64]
+        h.pald_tie_map_words.restype = i64
         for f in (h.pald_focus, h.pald_cohesion, h.pald_cohesion_noalloc, h.pald_batched, h.pald_host,
-                  h.pald_validate):
+                  h.pald_validate, h.pald_tie_map, h.pald_check_faults):
             f.restype = ctypes.c_int
         h.pald_status_string.argtypes = [ctypes.c_int]
         h.pald_status_string.restype = ctypes.c_char_p
@@ -206,6 +210,29 @@ def pald_validate(D, *, stream=None):
 
     n = D.shape[0]
     return _lib().pald_validate(_check(D, torch.float32, n, "D"), n, _stream_ptr(stream))
+
+
+def pald_tie_map_words(n: int) -> int:
+    return _lib().pald_tie_map_words(n)
+
+
+def pald_tie_map(D, *, stream=None):
+    """The tie map pass 2 uses for D (int32 view of the uint32 words; see pald.h)."""
+    import torch
+
+    n = D.shape[0]
+    words = pald_tie_map_words(n)
+    if words <= 0:
+        raise ValueError(f"n={n} out of range")
+    out = torch.empty(words, dtype=torch.int32, device=D.device)
+    st = _lib().pald_tie_map(_check(D, torch.float32, n, "D"), n, out.data_ptr(), _stream_ptr(stream))
+    _raise(st, "pald_tie_map")
+    return out
+
+
+def pald_check_faults(*, stream=None) -> int:
+    """Synchronise and return 0, or 7 (PALD_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
+    return _lib().pald_check_faults(_stream_ptr(stream))
 
 
 def pald_schedule_count() -> int:

@@ -11,26 +11,41 @@
 // points included.  R = 1/u is precomputed once per matrix (the reciprocal
 // loop between the passes, Sec. 6 figures), not in this kernel.
 //
-// Per (x, z, y) the inner loop issues six instructions, all of them exact
-// FP32 decisions on the input values:
-//     v2 = sat(d_zy * s + c) = w(b, d_zy)          FFMA.SAT     (FMA pipe)
-//     v1 = sat(d_xy * s + c) = w(b, d_xy)          FFMA.SAT     (FMA pipe)
-//     m  = min(v1, v2)                             FMNMX        (ALU pipe)
-//     p  = m > 0   (d_xz <= min(d_xy, d_zy))       FSETP        (ALU pipe)
-//     @p S_xz += v2 * r_xy                         FFMA         (FMA pipe)
-//     @p S_zx += v1 * r_zy                         FFMA         (FMA pipe)
-// (w(b, a) is 0 exactly when a < b, so the focus/support test needs no
-// separate copy of b.)
-// where (s, c) are per-pair constants built from b = d_xz so that
-// sat(a*s + c) = w(b, a) exactly: s = 2^(22-e) (2^(23-e) if b is a power of
-// two), c = 1/2 - b*s.  Then a == b gives exactly 1/2, and any other float a
-// is at least half a unit away from b*s after scaling, so saturation maps it
-// to 0 or 1.  b = 0 uses s = 2^127, c = 1/2 (inputs have no positive entry
-// below 2^-100).
+// Exact comparisons.  S = 2^(23 - e) is the matrix-wide power of two of
+// pass 1 (e the exponent of the smallest positive entry) and c = -b*S, with
+// b = d_xz, is the only per-pair constant.  For any entries a, b of the
+// matrix, t = a*S + c (one FFMA) is exactly 0 when a == b and at least 1 in
+// magnitude otherwise (a != b differ by at least one unit in the last place
+// of the smaller, which S scales to >= 1; a*S and b*S are exact).  Hence
+//     sat(t)             = [a > b]
+//     sat(t * 1/2 + 1/2) = w(b, a)        (0, 1/2 or 1, exactly)
+//
+// Long form, per (x, z, y), eight instructions:
+//     t2 = d_zy * S + c ;  t1 = d_xy * S + c        2 x FFMA     (FMA pipe)
+//     v2 = sat(t2/2 + 1/2) = w(b, d_zy) ; v1 = w(b, d_xy)
+//                                                  2 x FFMA.SAT (FMA pipe)
+//     m  = min(v1, v2) ;  p = m > 0                FMNMX, FSETP (ALU pipe)
+//       (w(b, a) is 0 exactly when a < b, so p is d_xz <= min(d_xy, d_zy))
+//     @p S_xz += v2 * r_xy ;  @p S_zx += v1 * r_zy 2 x FFMA     (FMA pipe)
+//
+// Short form, four instructions, for stages in which no one-sided tie
+// (d_xy == d_xz < d_zy, or d_zy == d_zx < d_xy) can occur:
+//     m  = min(d_xy, d_zy)                         FMNMX        (ALU pipe)
+//     v  = sat(m * S + c) = [m > b]                FFMA.SAT     (FMA pipe)
+//     S_xz += v * r_xy ;  S_zx += v * r_zy         2 x FFMA     (FMA pipe)
+// Without one-sided ties, b < m gives weight 1 to both sums and b > m gives
+// 0 to both.  b == m then needs d_xy == d_zy == d_xz with two equal entries
+// in row x or z (a marked tie, so not here), or y == z or y == x with
+// b == 0, where x == z and both r vanish (r_xx = 0) or the points are
+// duplicates (a marked tie again).  So every add that differs from the long
+// form adds +0, and both forms give the same bits.  Which stages may use the
+// short form comes from the tie map (one bit per 64 x 64 block pair and
+// 32 y; tie_map_core.cuh builds it).
 //
 // Accumulation (PALD_ACCUM_COMPENSATED): the pair {S_xz, S_zx} is an FP32
-// partial over 4 consecutive y.  Every 4 y it is folded into the running sums
-// {H_xz, H_zx}, which start at the bias B = 4: a partial never exceeds
+// partial over 4 consecutive y (fold_phase below places the chunk ends).
+// Every 4 y it is folded into the running sums {H_xz, H_zx}, which start at
+// the bias B = 4: a partial never exceeds
 // 4 * 1/2 plus the carried error, so |H| >= |S| always holds and Fast2Sum
 // (three adds, done as packed f32x2 ops on both accumulators at once) is
 // error-free.  Its exact error becomes the start of the next partial, so
@@ -51,36 +66,46 @@ struct CohesionSmem {
   static constexpr int FLOATS = kPipe * 2 * (Geo::SX + Geo::SY);  // kPipe stages of D_X, R_X, D_Z, R_Z
 };
 
-__device__ __forceinline__ void tie_constants(float b, float& s, float& c) {
-  const uint32_t bits = __float_as_uint(b);
-  if (bits == 0u) {
-    s = exp2i(127);
-    c = 0.5f;
-    return;
-  }
-  const int e = exponent_of(b);
-  const bool pow2 = (bits & 0x7fffffu) == 0u;
-  int k = (pow2 ? 23 : 22) - e;
-  k = k > 127 ? 127 : (k < -126 ? -126 : k);
-  s = exp2i(k);
-  c = __fsub_rn(0.5f, __fmul_rn(b, s));  // b*s is exact (power-of-two scaling)
-}
-
-// One (x, z, y) step on the packed partial {S_xz, S_zx}; see the header.
-__device__ __forceinline__ void cohesion_step(uint64_t& sacc, float a1, float a2, float s, float c, float r1,
+// Long form of one (x, z, y) step on the packed partial {S_xz, S_zx}.
+__device__ __forceinline__ void cohesion_step(uint64_t& sacc, float a1, float a2, float S, float c, float r1,
                                               float r2) {
-  asm("{\n\t.reg .pred p;\n\t.reg .f32 m, v1, v2, sx, sz;\n\t"
+  asm("{\n\t.reg .pred p;\n\t.reg .f32 m, t1, t2, v1, v2, sx, sz;\n\t"
       "mov.b64 {sx, sz}, %0;\n\t"
-      "fma.rn.sat.f32 v2, %2, %3, %4;\n\t"
-      "fma.rn.sat.f32 v1, %1, %3, %4;\n\t"
+      "fma.rn.f32 t2, %2, %3, %4;\n\t"
+      "fma.rn.f32 t1, %1, %3, %4;\n\t"
+      "fma.rn.sat.f32 v2, t2, 0f3F000000, 0f3F000000;\n\t"
+      "fma.rn.sat.f32 v1, t1, 0f3F000000, 0f3F000000;\n\t"
       "min.f32 m, v1, v2;\n\t"
       "setp.gt.f32 p, m, 0f00000000;\n\t"
       "@p fma.rn.f32 sx, v2, %5, sx;\n\t"
       "@p fma.rn.f32 sz, v1, %6, sz;\n\t"
       "mov.b64 %0, {sx, sz};\n\t}"
       : "+l"(sacc)
-      : "f"(a1), "f"(a2), "f"(s), "f"(c), "f"(r1), "f"(r2));
+      : "f"(a1), "f"(a2), "f"(S), "f"(c), "f"(r1), "f"(r2));
 }
+
+// Short form of one (x, z, y) step (no one-sided tie possible).
+__device__ __forceinline__ void cohesion_step_short(uint64_t& sacc, float a1, float a2, float S, float c, float r1,
+                                                    float r2) {
+  asm("{\n\t.reg .f32 m, v, sx, sz;\n\t"
+      "mov.b64 {sx, sz}, %0;\n\t"
+      "min.f32 m, %1, %2;\n\t"
+      "fma.rn.sat.f32 v, m, %3, %4;\n\t"
+      "fma.rn.f32 sx, v, %5, sx;\n\t"
+      "fma.rn.f32 sz, v, %6, sz;\n\t"
+      "mov.b64 %0, {sx, sz};\n\t}"
+      : "+l"(sacc)
+      : "f"(a1), "f"(a2), "f"(S), "f"(c), "f"(r1), "f"(r2));
+}
+
+// Fold phase of the pair in row slot i and column slot j of a thread tile:
+// 3 when x + z is even, 1 when it is odd, for the pair's global (x, z).
+// Every geometry puts x == i and z == j (mod 2) (tile_geom.cuh), so this is
+// a compile-time constant per slot.  It must be symmetric in x and z:
+// depending on the tile size, c_zx is the zx lane of pair (x, z) or the xz
+// lane of pair (z, x), and a symmetric phase gives both the same chunking,
+// so every schedule, both forms and the batched path stay bit-identical.
+__host__ __device__ constexpr int fold_phase(int i, int j) { return ((i + j) & 1) ? 1 : 3; }
 
 // Packed f32x2 add and subtract (one instruction for both lanes).
 __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
@@ -112,14 +137,161 @@ __device__ __forceinline__ void unpack2(uint64_t v, float& lo, float& hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
+// One pipeline stage (BK consecutive y) of a CTA tile, long or short form.
+template <class Geo, int MODE, bool SHORT>
+__device__ __forceinline__ void cohesion_stage(const float* ad, const float* ar, const float* bd, const float* br,
+                                               int tx, int tz, float S, const float (&cv)[Geo::TX][Geo::TY],
+                                               uint64_t (&sacc)[Geo::TX][Geo::TY],
+                                               uint64_t (&hacc)[Geo::TX][Geo::TY]) {
+  constexpr int TX = Geo::TX, TY = Geo::TY;
+#pragma unroll Geo::UNR
+  for (int kk = 0; kk < Geo::BK; ++kk) {
+    float a1[TX], r1[TX], a2[TY], r2[TY];
+#pragma unroll
+    for (int g = 0; g < Geo::GX; ++g) {
+      lds<4>(ad + kk * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
+      lds<4>(ar + kk * Geo::BX + Geo::row_off(tx, 4 * g), r1 + 4 * g);
+    }
+#pragma unroll
+    for (int g = 0; g < Geo::GY; ++g) {
+      lds<Geo::CW>(bd + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), a2 + Geo::CW * g);
+      lds<Geo::CW>(br + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), r2 + Geo::CW * g);
+    }
+#pragma unroll
+    for (int i = 0; i < TX; ++i)
+#pragma unroll
+      for (int j = 0; j < TY; ++j) {
+        if (SHORT)
+          cohesion_step_short(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
+        else
+          cohesion_step(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
+      }
+    if (MODE == PALD_ACCUM_COMPENSATED) {
+      // pair (x, z) folds after the y with y mod 4 == fold_phase(i, j):
+      // half of a thread's pairs fold at each of two y in four, spreading
+      // the packed adds over the FMA pipe
+#pragma unroll
+      for (int i = 0; i < TX; ++i)
+#pragma unroll
+        for (int j = 0; j < TY; ++j)
+          if ((kk % kMergeEvery) == fold_phase(i, j)) fast2sum_fold(hacc[i][j], sacc[i][j]);
+    }
+  }
+}
+
+// Reads the tie-map row of one tile's block pair: tied(st) is nonzero when
+// stage st (y = st*BK .. st*BK+BK-1) must take the long form.  Uniform over
+// the CTA.  A null map, or a dirty block on either side, means "always".
+template <int BK>
+struct TieCursor {
+  const uint32_t* row;
+  int64_t nstages;
+  bool all_long;
+  __device__ __forceinline__ TieCursor(const uint32_t* tmap, int64_t n, int64_t X0, int64_t Z0) {
+    const TieMapDims dm = tie_map_dims(n);
+    const int64_t bx = X0 / kTieBlock, bz = Z0 / kTieBlock;
+    row = tmap + (bx * dm.nb + bz) * dm.wpp;
+    nstages = (n + BK - 1) / BK;
+    all_long = tmap == nullptr || __ldg(tmap + dm.nb * dm.nb * dm.wpp + bx) != 0u ||
+               __ldg(tmap + dm.nb * dm.nb * dm.wpp + bz) != 0u;
+  }
+  __device__ __forceinline__ uint32_t tied(int64_t st) const {
+    constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
+    if (all_long) return 1u;
+    if (st >= nstages) return 0u;
+    const int64_t g = (st * BK) / kTieGroup;
+    return (__ldg(row + (g >> 5)) >> (g & 31)) & kGroupMask;
+  }
+};
+
+// Per-pair constants c = -d_xz * S and the zeroed accumulators.
+template <class Geo>
+__device__ __forceinline__ void cohesion_init(const float* __restrict__ D, int64_t n, int64_t X0, int64_t Z0, int tx,
+                                              int tz, float S, float (&cv)[Geo::TX][Geo::TY],
+                                              uint64_t (&sacc)[Geo::TX][Geo::TY],
+                                              uint64_t (&hacc)[Geo::TX][Geo::TY]) {
+#pragma unroll
+  for (int i = 0; i < Geo::TX; ++i) {
+    const int64_t x = X0 + Geo::row_off(tx, i);
+#pragma unroll
+    for (int j = 0; j < Geo::TY; ++j) {
+      const int64_t z = Z0 + Geo::col_off(tz, j);
+      cv[i][j] = __fmul_rn(-((x < n && z < n) ? __ldg(D + x * n + z) : 0.f), S);  // exact: power of two
+    }
+  }
+  const uint64_t zero2 = pack2(0.f, 0.f);
+  const uint64_t bias2 = pack2(kMergeBias, kMergeBias);
+#pragma unroll
+  for (int i = 0; i < Geo::TX; ++i)
+#pragma unroll
+    for (int j = 0; j < Geo::TY; ++j) {
+      sacc[i][j] = zero2;
+      hacc[i][j] = bias2;
+    }
+}
+
+// Final merge and stores of C[X, Z] (and of C[Z, X] when `mirror`).
+template <class Geo, int MODE>
+__device__ __forceinline__ void cohesion_finish(float* __restrict__ C, int64_t n, int64_t X0, int64_t Z0, int tx,
+                                                int tz, bool mirror, bool vec,
+                                                const uint64_t (&sacc)[Geo::TX][Geo::TY],
+                                                const uint64_t (&hacc)[Geo::TX][Geo::TY]) {
+  const double inv = 1.0 / static_cast<double>(n - 1);
+  // value of the (xz or zx) lane: compensated (H - B) + S in FP64, or plain S
+  auto finish = [&](uint64_t h2, uint64_t s2, bool zx) -> float {
+    float hl, hh, sl, sh;
+    unpack2(h2, hl, hh);
+    unpack2(s2, sl, sh);
+    const float h = zx ? hh : hl, s = zx ? sh : sl;
+    if (MODE == PALD_ACCUM_COMPENSATED)
+      return static_cast<float>(((static_cast<double>(h) - static_cast<double>(kMergeBias)) +
+                                 static_cast<double>(s)) * inv);
+    return static_cast<float>(static_cast<double>(s) * inv);
+  };
+#pragma unroll
+  for (int i = 0; i < Geo::TX; ++i) {
+    const int64_t x = X0 + Geo::row_off(tx, i);
+#pragma unroll
+    for (int gj = 0; gj < Geo::GY; ++gj) {
+      float v[Geo::CW];
+#pragma unroll
+      for (int k = 0; k < Geo::CW; ++k) v[k] = finish(hacc[i][Geo::CW * gj + k], sacc[i][Geo::CW * gj + k], false);
+      storew<Geo::CW>(C, n, x, Z0 + Geo::col_off(tz, Geo::CW * gj), v, vec);
+    }
+  }
+  if (mirror) {
+#pragma unroll
+    for (int j = 0; j < Geo::TY; ++j) {
+      const int64_t z = Z0 + Geo::col_off(tz, j);
+#pragma unroll
+      for (int gi = 0; gi < Geo::GX; ++gi) {
+        float v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = finish(hacc[4 * gi + k][j], sacc[4 * gi + k][j], true);
+        storew<4>(C, n, z, X0 + Geo::row_off(tx, 4 * gi), v, vec);
+      }
+    }
+  }
+}
+
+template <class Geo>
+__device__ __forceinline__ void cohesion_tile_checks() {
+  static_assert(Geo::BK % kMergeEvery == 0, "stages must hold whole merge chunks");
+  static_assert(Geo::B <= kTieBlock && kTieBlock % Geo::B == 0, "a tile must lie in one tie-map block pair");
+  static_assert(Geo::BK == 16 || Geo::BK == 32 || Geo::BK == 64, "stage depth must tile the tie-map y groups");
+}
+
 // Computes C[X, Z] (and C[Z, X] off the diagonal) for super-tile (bi, bj),
-// column slice `slice`.  `smem` holds CohesionSmem<Geo>::FLOATS floats.
+// column slice `slice`, staging operands with per-thread cp.async copies.
+// `smem` holds CohesionSmem<Geo>::FLOATS floats.  `tmap` is the matrix's
+// tie map (null: long form everywhere); S its pass-1 scale (focus_scale).
 // Must be called by all Geo::NT threads.
 template <class Geo, int MODE>
 __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const float* __restrict__ R, int64_t n,
-                                              float* __restrict__ C, int bi, int bj, int slice, float* smem) {
+                                              float* __restrict__ C, const uint32_t* __restrict__ tmap, float S,
+                                              int bi, int bj, int slice, float* smem) {
   constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY, NT = Geo::NT;
-  static_assert(BK % kMergeEvery == 0, "stages must hold whole merge chunks");
+  cohesion_tile_checks<Geo>();
   const int64_t X0 = static_cast<int64_t>(bi) * Geo::B;
   const int64_t Z0 = static_cast<int64_t>(bj) * Geo::B + static_cast<int64_t>(slice) * Geo::BY;
   const int tx = threadIdx.x % Geo::TPX, tz = threadIdx.x / Geo::TPX;
@@ -144,105 +316,144 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
     cp_async_commit();
   }
 
-  float sv[TX][TY], cv[TX][TY];
+  const TieCursor<BK> ties(tmap, n, X0, Z0);
+  uint32_t tie_next = ties.tied(0);
+
+  float cv[TX][TY];
   uint64_t sacc[TX][TY], hacc[TX][TY];
-#pragma unroll
-  for (int i = 0; i < TX; ++i) {
-    const int64_t x = X0 + Geo::row_off(tx, i);
-#pragma unroll
-    for (int j = 0; j < TY; ++j) {
-      const int64_t z = Z0 + Geo::col_off(tz, j);
-      tie_constants((x < n && z < n) ? __ldg(D + x * n + z) : 0.f, sv[i][j], cv[i][j]);
-    }
-  }
-  const uint64_t zero2 = pack2(0.f, 0.f);
-  const uint64_t bias2 = pack2(kMergeBias, kMergeBias);
-#pragma unroll
-  for (int i = 0; i < TX; ++i)
-#pragma unroll
-    for (int j = 0; j < TY; ++j) {
-      sacc[i][j] = zero2;
-      hacc[i][j] = bias2;
-    }
+  cohesion_init<Geo>(D, n, X0, Z0, tx, tz, S, cv, sacc, hacc);
 
   for (int64_t st = 0; st < nstages; ++st) {
     const int buf = static_cast<int>(st % kPipe);
-    cp_async_wait<kPipe - 2>();  // stage st has landed (later ones may be in flight)
-    __syncthreads();             // ... for every thread, and stage st-1's buffer is free
+    const uint32_t tie_now = tie_next;
+    tie_next = ties.tied(st + 1);  // loaded a stage ahead of its use
+    cp_async_wait<kPipe - 2>();    // stage st has landed (later ones may be in flight)
+    __syncthreads();               // ... for every thread, and stage st-1's buffer is free
     if (st + kPipe - 1 < nstages) stage(static_cast<int>((st + kPipe - 1) % kPipe), (st + kPipe - 1) * BK);
     cp_async_commit();  // possibly empty: keeps one group per stage
     const float* ad = Ad + buf * Geo::SX;
     const float* ar = Ar + buf * Geo::SX;
     const float* bd = Bd + buf * Geo::SY;
     const float* br = Br + buf * Geo::SY;
-#pragma unroll Geo::UNR
-    for (int kk = 0; kk < BK; ++kk) {
-      float a1[TX], r1[TX], a2[TY], r2[TY];
-#pragma unroll
-      for (int g = 0; g < Geo::GX; ++g) {
-        lds<4>(ad + kk * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
-        lds<4>(ar + kk * Geo::BX + Geo::row_off(tx, 4 * g), r1 + 4 * g);
-      }
-#pragma unroll
-      for (int g = 0; g < Geo::GY; ++g) {
-        lds<Geo::CW>(bd + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), a2 + Geo::CW * g);
-        lds<Geo::CW>(br + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), r2 + Geo::CW * g);
-      }
-#pragma unroll
-      for (int i = 0; i < TX; ++i)
-#pragma unroll
-        for (int j = 0; j < TY; ++j)
-          cohesion_step(sacc[i][j], a1[i], a2[j], sv[i][j], cv[i][j], r1[i], r2[j]);
-      if (MODE == PALD_ACCUM_COMPENSATED) {
-        // every pair folds at the same y (y mod 4 == 3): the chunking is
-        // then the same for every schedule, for both lanes of a pair and
-        // for the batched path, so all of them give bit-identical C
-        if ((kk % kMergeEvery) == kMergeEvery - 1) {
-#pragma unroll
-          for (int i = 0; i < TX; ++i)
-#pragma unroll
-            for (int j = 0; j < TY; ++j) fast2sum_fold(hacc[i][j], sacc[i][j]);
-        }
-      }
-    }
+    if (tie_now)
+      cohesion_stage<Geo, MODE, false>(ad, ar, bd, br, tx, tz, S, cv, sacc, hacc);
+    else
+      cohesion_stage<Geo, MODE, true>(ad, ar, bd, br, tx, tz, S, cv, sacc, hacc);
   }
+  cohesion_finish<Geo, MODE>(C, n, X0, Z0, tx, tz, bi != bj, vec, sacc, hacc);
+}
 
-  const double inv = 1.0 / static_cast<double>(n - 1);
-  // value of the (xz or zx) lane: compensated (H - B) + S in FP64, or plain S
-  auto finish = [&](uint64_t h2, uint64_t s2, bool zx) -> float {
-    float hl, hh, sl, sh;
-    unpack2(h2, hl, hh);
-    unpack2(s2, sl, sh);
-    const float h = zx ? hh : hl, s = zx ? sh : sl;
-    if (MODE == PALD_ACCUM_COMPENSATED)
-      return static_cast<float>(((static_cast<double>(h) - static_cast<double>(kMergeBias)) +
-                                 static_cast<double>(s)) * inv);
-    return static_cast<float>(static_cast<double>(s) * inv);
+// ---------------------------------------------------------------------------
+// TMA-staged tile.  One thread issues four tensor copies per stage (the D and
+// R panels of X and Z, each BK rows x 64 columns, zero-filled outside the
+// matrix) that complete on the buffer's mbarrier; every thread waits on it
+// with a time limit.  One CTA barrier per stage keeps all warps on the same
+// stage, hence on the same (short or long) loop body, which matters for the
+// instruction cache.  No per-thread copy arithmetic remains in the loop, and
+// the kernel fits two CTAs per SM (four warps per scheduler).  Requires
+// 64 x 64 tiles, n % 4 == 0 and 16-byte aligned D and R (the TMA row pitch).
+
+constexpr int kTmaStages = 3;
+constexpr int kTieWordsMax = 1024;  // tie-map words of one block pair for n <= 2^20
+
+template <class Geo>
+struct CohesionTmaSmem {
+  static constexpr int PANEL = Geo::BK * 64;  // floats of one panel stage
+  static constexpr int FLOATS = kTmaStages * 4 * PANEL;
+  // panels, mbarriers, the tile's tie-map words, alignment slack
+  static constexpr int bytes(int64_t n) {
+    return FLOATS * 4 + 8 * kTmaStages + 4 * static_cast<int>(tie_map_dims(n).wpp) + 128;
+  }
+  static constexpr int MAX_BYTES = FLOATS * 4 + 8 * kTmaStages + 4 * kTieWordsMax + 128;
+};
+
+// Returns false (and the caller records a fault) when a wait ran out of
+// time; the CTA then stops early and its outputs are unspecified.
+template <class Geo, int MODE>
+__device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const CUtensorMap* tmR, int64_t n,
+                                                  float* __restrict__ C, const float* __restrict__ D,
+                                                  const uint32_t* __restrict__ tmap, float S, int bi, int bj,
+                                                  float* smem_raw) {
+  constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY, NT = Geo::NT;
+  constexpr int PANEL = CohesionTmaSmem<Geo>::PANEL;
+  static_assert(Geo::BX == 64 && Geo::BY == 64, "TMA tiles are 64 x 64");
+  cohesion_tile_checks<Geo>();
+  const int tx = threadIdx.x % Geo::TPX, tz = threadIdx.x / Geo::TPX;
+  const int nstages = static_cast<int>((n + BK - 1) / BK);
+
+  // 128-byte aligned panels, the mbarriers, the tie words (offsets from the
+  // shared array itself, so the compiler keeps shared-memory loads)
+  const int pad = static_cast<int>((128u - (smem_u32(smem_raw) & 127u)) & 127u) / 4;
+  float* panels = smem_raw + pad;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(panels + CohesionTmaSmem<Geo>::FLOATS);
+  uint32_t* tie_words = reinterpret_cast<uint32_t*>(bars + kTmaStages);
+  auto panel = [&](int buf, int k) { return panels + (buf * 4 + k) * PANEL; };  // k: Ad, Ar, Bd, Br
+
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int b = 0; b < kTmaStages; ++b) mbar_init(smem_u32(bars + b), 1);
+    mbar_fence_init();
+  }
+  // the tile's tie-map row (all ones when there is no map or a block is dirty)
+  {
+    const TieMapDims dm = tie_map_dims(n);
+    const int64_t bx = bi, bz = bj;  // 64-wide tiles are the map's blocks
+    const bool all_long = tmap == nullptr || __ldg(tmap + dm.nb * dm.nb * dm.wpp + bx) != 0u ||
+                          __ldg(tmap + dm.nb * dm.nb * dm.wpp + bz) != 0u;
+    const uint32_t* row = tmap + (bx * dm.nb + bz) * dm.wpp;
+    for (int w = threadIdx.x; w < dm.wpp; w += NT) tie_words[w] = all_long ? ~0u : __ldg(row + w);
+  }
+  __syncthreads();
+  auto issue = [&](int q) {  // stage q into buffer q % kTmaStages (one thread)
+    const int buf = q % kTmaStages;
+    const uint32_t bar = smem_u32(bars + buf);
+    const int y0 = q * BK;
+    mbar_expect_tx(bar, 4u * PANEL * sizeof(float));
+    tma_load_2d(smem_u32(panel(buf, 0)), tmD, bi * 64, y0, bar);
+    tma_load_2d(smem_u32(panel(buf, 1)), tmR, bi * 64, y0, bar);
+    tma_load_2d(smem_u32(panel(buf, 2)), tmD, bj * 64, y0, bar);
+    tma_load_2d(smem_u32(panel(buf, 3)), tmR, bj * 64, y0, bar);
   };
-#pragma unroll
-  for (int i = 0; i < TX; ++i) {
-    const int64_t x = X0 + Geo::row_off(tx, i);
-#pragma unroll
-    for (int gj = 0; gj < Geo::GY; ++gj) {
-      float v[Geo::CW];
-#pragma unroll
-      for (int k = 0; k < Geo::CW; ++k) v[k] = finish(hacc[i][Geo::CW * gj + k], sacc[i][Geo::CW * gj + k], false);
-      storew<Geo::CW>(C, n, x, Z0 + Geo::col_off(tz, Geo::CW * gj), v, vec);
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kTmaStages - 1 && q < nstages; ++q) issue(q);
+
+  float cv[TX][TY];
+  uint64_t sacc[TX][TY], hacc[TX][TY];
+  cohesion_init<Geo>(D, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, tz, S, cv, sacc, hacc);
+
+  constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
+  int st = 0;
+  bool aborted = false;
+  for (; st < nstages; ++st) {
+    const int buf = st % kTmaStages;
+    const bool ok = mbar_wait_bounded(smem_u32(bars + buf), static_cast<uint32_t>((st / kTmaStages) & 1));
+    // one barrier per stage: stage st has landed for every thread (or some
+    // thread gave up), and every thread is done with stage st-1's buffer
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
     }
+    if (threadIdx.x == 0 && st + kTmaStages - 1 < nstages) issue(st + kTmaStages - 1);
+    const int g = st * BK / kTieGroup;
+    if ((tie_words[g >> 5] >> (g & 31)) & kGroupMask)
+      cohesion_stage<Geo, MODE, false>(panel(buf, 0), panel(buf, 1), panel(buf, 2), panel(buf, 3), tx, tz, S, cv,
+                                       sacc, hacc);
+    else
+      cohesion_stage<Geo, MODE, true>(panel(buf, 0), panel(buf, 1), panel(buf, 2), panel(buf, 3), tx, tz, S, cv,
+                                      sacc, hacc);
   }
-  if (bi != bj) {
-#pragma unroll
-    for (int j = 0; j < TY; ++j) {
-      const int64_t z = Z0 + Geo::col_off(tz, j);
-#pragma unroll
-      for (int gi = 0; gi < Geo::GX; ++gi) {
-        float v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = finish(hacc[4 * gi + k][j], sacc[4 * gi + k][j], true);
-        storew<4>(C, n, z, X0 + Geo::row_off(tx, 4 * gi), v, vec);
-      }
+  if (aborted) {
+    // let the copies already issued (stages st .. st+kTmaStages-2) land
+    // before the CTA's shared memory is released, each wait again bounded
+    if (threadIdx.x == 0) {
+      for (int q = st; q < st + kTmaStages - 1 && q < nstages; ++q)
+        mbar_wait_bounded(smem_u32(bars + q % kTmaStages), static_cast<uint32_t>((q / kTmaStages) & 1));
     }
+    __syncthreads();
+    return false;
   }
+  cohesion_finish<Geo, MODE>(C, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, tz, bi != bj, true, sacc, hacc);
+  return true;
 }
 
 // R[row][col] = 1/u (correctly rounded FP32), 0 on the diagonal and where

@@ -97,19 +97,21 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
   if (!D || !U || !C || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
   const pald_opts o = opts_or_default(opts);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  // scratch: the scan summary (validation only) and R = 1/u, n x n FP32
+  // scratch: R = 1/u (n x n FP32), the tie map, the scan summary
   const size_t rbytes = static_cast<size_t>(n) * static_cast<size_t>(n) * sizeof(float);
+  const size_t tbytes = (static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t) + 255) / 256 * 256;
   Scratch scratch(s);
-  cudaError_t e = scratch.alloc(rbytes + 256);
+  cudaError_t e = scratch.alloc(rbytes + tbytes + 256);
   if (e != cudaSuccess) return cuda_fail(e);
   float* R = static_cast<float*>(scratch.p);
-  if (o.validate) {
-    auto* scan = reinterpret_cast<ScanResult*>(static_cast<char*>(scratch.p) + rbytes);
-    pald_status st = scan_and_check(D, n, scan, true, s);
-    if (st != PALD_OK) return st;
-  }
+  auto* tmap = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch.p) + rbytes);
+  auto* scan = reinterpret_cast<ScanResult*>(static_cast<char*>(scratch.p) + rbytes + tbytes);
+  pald_status st = scan_and_check(D, n, scan, o.validate != 0, s);
+  if (st != PALD_OK) return st;
+  if ((e = launch_tie_map(D, n, tmap, s)) != cudaSuccess) return cuda_fail(e);
   if ((e = launch_reciprocal(U, R, n, s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_cohesion(D, R, n, C, o.accum_mode, o.schedule_id, s)) != cudaSuccess) return cuda_fail(e);
+  if ((e = launch_cohesion(D, R, n, C, tmap, scan, o.accum_mode, o.schedule_id, s)) != cudaSuccess)
+    return cuda_fail(e);
   return PALD_OK;
 }
 
@@ -157,6 +159,21 @@ pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_
   return PALD_OK;
 }
 
+int64_t pald_tie_map_words(int64_t n) { return (n < 2 || n > kMaxN) ? 0 : tie_map_words(n); }
+
+pald_status pald_tie_map(const float* D, int64_t n, uint32_t* map, pald_stream_t stream) {
+  if (!D || !map || n < 2 || n > kMaxN) return PALD_ERR_INVALID_ARG;
+  cudaError_t e = launch_tie_map(D, n, map, reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PALD_OK : cuda_fail(e);
+}
+
+pald_status pald_check_faults(pald_stream_t stream) {
+  uint32_t faults = 0;
+  cudaError_t e = take_cohesion_faults(&faults, reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e);
+  return faults ? PALD_ERR_TIMEOUT : PALD_OK;
+}
+
 int32_t pald_schedule_count(void) { return kScheduleCount; }
 
 const char* pald_schedule_name(int32_t id) {
@@ -168,6 +185,7 @@ const char* pald_schedule_name(int32_t id) {
     case 4: return "focus 64x32 slices, 4x4, 32-deep | cohesion 64x32 slices, 4x2, 32-deep";
     case 5: return "focus 64x64, 4x4, 64-deep stages unrolled 16 | cohesion 64x64, 4x4, 32-deep unrolled 4";
     case 6: return "focus 128x64 slices, 8x4, 32-deep | cohesion 64x64, 4x4, 64-deep unrolled 8";
+    case 7: return "focus as 2 | cohesion 64x64, 4x4, 32-deep, TMA-staged, 2 CTAs/SM (needs n % 4 == 0)";
     default: return nullptr;
   }
 }

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(CG::NT) batched_cohesion_kernel(const float* _
                                                                   const float* __restrict__ R,
                                                                   float* __restrict__ C,
                                                                   const MatrixDesc* __restrict__ mats,
+                                                                  const ScanResult* __restrict__ scans,
                                                                   const WorkItem* __restrict__ items,
                                                                   int64_t n_items, int* counter) {
   extern __shared__ __align__(16) float smem[];
@@ -108,7 +109,8 @@ __global__ void __launch_bounds__(CG::NT) batched_cohesion_kernel(const float* _
     if (it >= n_items) break;
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
-    cohesion_tile<CG, MODE>(D + md.off, R + md.off, md.n, C + md.off, w.bi, w.bj, w.slice, smem);
+    const float S = focus_scale(scans[w.matrix].inv_min_pos_bits);
+    cohesion_tile<CG, MODE>(D + md.off, R + md.off, md.n, C + md.off, nullptr, S, w.bi, w.bj, w.slice, smem);
   }
 }
 
@@ -243,10 +245,10 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     batched_reciprocal_kernel<<<dim3(8, count), 256, 0, cs>>>(U, d_recip, d_mats);
     if (plain)
       batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, csmem, cs>>>(
-          D, d_recip, C, d_mats, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
+          D, d_recip, C, d_mats, d_scans, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
     else
       batched_cohesion_kernel<PALD_ACCUM_COMPENSATED><<<gc, CG::NT, csmem, cs>>>(
-          D, d_recip, C, d_mats, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
+          D, d_recip, C, d_mats, d_scans, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
     cudaError_t launch_err = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &p.graph);
     if (e == cudaSuccess && launch_err != cudaSuccess) e = launch_err;

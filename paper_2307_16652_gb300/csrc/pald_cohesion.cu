@@ -1,6 +1,9 @@
 // Pass 2 (cohesion) for one matrix: a row-parallel kernel forms R = 1/u with
 // a zero diagonal, then one CTA per upper-triangle super-tile slice (X <= Z)
-// computes both C[X, Z] and C[Z, X] from the same comparisons.
+// computes both C[X, Z] and C[Z, X] from the same comparisons, each stage in
+// the short or the long form as the tie map says.
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
+
 #include "cohesion_core.cuh"
 #include "schedules.cuh"
 
@@ -18,15 +21,16 @@ __global__ void __launch_bounds__(256) reciprocal_kernel(const int32_t* __restri
 template <class Geo, int MODE, int MINB>
 __global__ void __launch_bounds__(Geo::NT, MINB)
     cohesion_kernel(const float* __restrict__ D, const float* __restrict__ R, int64_t n, float* __restrict__ C,
-                    int64_t T) {
+                    const uint32_t* __restrict__ tmap, const ScanResult* __restrict__ scan, int64_t T) {
   extern __shared__ __align__(16) float smem[];
   int bi, bj, slice;
   decode_tile(blockIdx.x, T, Geo::H, &bi, &bj, &slice);
-  cohesion_tile<Geo, MODE>(D, R, n, C, bi, bj, slice, smem);
+  cohesion_tile<Geo, MODE>(D, R, n, C, tmap, focus_scale(scan->inv_min_pos_bits), bi, bj, slice, smem);
 }
 
 template <class Geo, int MODE, int MINB>
-cudaError_t launch_t(const float* D, const float* R, int64_t n, float* C, cudaStream_t s) {
+cudaError_t launch_t(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+                     const ScanResult* scan, cudaStream_t s) {
   const int64_t T = (n + Geo::B - 1) / Geo::B;
   const int64_t ctas = T * (T + 1) / 2 * Geo::H;
   if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
@@ -38,20 +42,69 @@ cudaError_t launch_t(const float* D, const float* R, int64_t n, float* C, cudaSt
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  cohesion_kernel<Geo, MODE, MINB><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(D, R, n, C, T);
+  cohesion_kernel<Geo, MODE, MINB><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(D, R, n, C, tmap, scan, T);
+  return cudaGetLastError();
+}
+
+// Set by a CTA whose bounded wait gave up (never in normal operation).
+__device__ uint32_t g_cohesion_faults;
+
+template <int MODE>
+__global__ void __launch_bounds__(CohesionS7::NT, 2)
+    cohesion_tma_kernel(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmR,
+                        const float* __restrict__ D, int64_t n, float* __restrict__ C,
+                        const uint32_t* __restrict__ tmap, const ScanResult* __restrict__ scan, int64_t T) {
+  extern __shared__ __align__(128) float smem_tma[];
+  int bi, bj, slice;
+  decode_tile(blockIdx.x, T, 1, &bi, &bj, &slice);
+  const float S = focus_scale(scan->inv_min_pos_bits);
+  if (!cohesion_tile_tma<CohesionS7, MODE>(&tmD, &tmR, n, C, D, tmap, S, bi, bj, smem_tma) && threadIdx.x == 0)
+    atomicOr(&g_cohesion_faults, 1u);
+}
+
+// The TMA path needs the row pitch and the base addresses 16-byte aligned.
+bool tma_ok(const float* D, const float* R, const float* C, int64_t n) {
+  return n >= 64 && n % 4 == 0 && reinterpret_cast<uintptr_t>(D) % 16 == 0 &&
+         reinterpret_cast<uintptr_t>(R) % 16 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0;
+}
+
+template <int MODE>
+cudaError_t launch_tma(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+                       const ScanResult* scan, cudaStream_t s) {
+  using Geo = CohesionS7;
+  const int64_t T = (n + 63) / 64;
+  const int64_t ctas = T * (T + 1) / 2;
+  if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
+  CUtensorMap mD, mR;
+  cudaError_t e = encode_panel_map(&mD, D, n, Geo::BK);
+  if (e == cudaSuccess) e = encode_panel_map(&mR, R, n, Geo::BK);
+  if (e != cudaSuccess) return e;
+  const int smem = CohesionTmaSmem<Geo>::bytes(n);
+  static bool attr_set = false;  // idempotent: racing setters write the same value
+  if (!attr_set) {
+    e = cudaFuncSetAttribute(cohesion_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             CohesionTmaSmem<Geo>::MAX_BYTES);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cohesion_tma_kernel<MODE><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(mD, mR, D, n, C, tmap, scan, T);
   return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t launch_mode(const float* D, const float* R, int64_t n, float* C, int schedule, cudaStream_t s) {
+cudaError_t launch_mode(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+                        const ScanResult* scan, int schedule, cudaStream_t s) {
   switch (schedule) {
-    case 0: return launch_t<CohesionS0, MODE, 1>(D, R, n, C, s);
-    case 1: return launch_t<CohesionS1, MODE, 4>(D, R, n, C, s);
-    case 2: return launch_t<CohesionS2, MODE, 2>(D, R, n, C, s);
-    case 3: return launch_t<CohesionS3, MODE, 1>(D, R, n, C, s);
-    case 4: return launch_t<CohesionS4, MODE, 2>(D, R, n, C, s);
-    case 5: return launch_t<CohesionS5, MODE, 1>(D, R, n, C, s);
-    case 6: return launch_t<CohesionS6, MODE, 1>(D, R, n, C, s);
+    case 0: return launch_t<CohesionS0, MODE, 1>(D, R, n, C, tmap, scan, s);
+    case 1: return launch_t<CohesionS1, MODE, 4>(D, R, n, C, tmap, scan, s);
+    case 2: return launch_t<CohesionS2, MODE, 2>(D, R, n, C, tmap, scan, s);
+    case 3: return launch_t<CohesionS3, MODE, 1>(D, R, n, C, tmap, scan, s);
+    case 4: return launch_t<CohesionS4, MODE, 2>(D, R, n, C, tmap, scan, s);
+    case 5: return launch_t<CohesionS5, MODE, 1>(D, R, n, C, tmap, scan, s);
+    case 6: return launch_t<CohesionS6, MODE, 1>(D, R, n, C, tmap, scan, s);
+    case 7:
+      if (tma_ok(D, R, C, n)) return launch_tma<MODE>(D, R, n, C, tmap, scan, s);
+      return launch_t<CohesionS3, MODE, 1>(D, R, n, C, tmap, scan, s);  // same tile with per-thread copies
     default: return cudaErrorInvalidValue;
   }
 }
@@ -65,11 +118,41 @@ cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, int accum_mode, int schedule,
-                            cudaStream_t s) {
+cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s) {
+  uint32_t zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_cohesion_faults, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && *out != 0u)
+    e = cudaMemcpyToSymbolAsync(g_cohesion_faults, &zero, sizeof(uint32_t), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
+
+cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};  // {columns, rows}
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(n) * sizeof(float)};           // row pitch, bytes
+  const cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(rows)};
+  const cuuint32_t elem[2] = {1u, 1u};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
+                            elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+                            const ScanResult* scan, int accum_mode, int schedule, cudaStream_t s) {
   if (schedule < 0) schedule = default_cohesion_schedule(n);
-  if (accum_mode == PALD_ACCUM_PLAIN) return launch_mode<PALD_ACCUM_PLAIN>(D, R, n, C, schedule, s);
-  return launch_mode<PALD_ACCUM_COMPENSATED>(D, R, n, C, schedule, s);
+  if (accum_mode == PALD_ACCUM_PLAIN) return launch_mode<PALD_ACCUM_PLAIN>(D, R, n, C, tmap, scan, schedule, s);
+  return launch_mode<PALD_ACCUM_COMPENSATED>(D, R, n, C, tmap, scan, schedule, s);
 }
 
 }  // namespace pald

@@ -47,6 +47,7 @@ cudaError_t launch_focus(const float* D, int64_t n, int32_t* U, const ScanResult
     case 4: return launch_t<FocusS4, 4>(D, n, U, scan, s);
     case 5: return launch_t<FocusS5, 2>(D, n, U, scan, s);
     case 6: return launch_t<FocusS6, 1>(D, n, U, scan, s);
+    case 7: return launch_t<FocusS7, 2>(D, n, U, scan, s);
     default: return cudaErrorInvalidValue;
   }
 }

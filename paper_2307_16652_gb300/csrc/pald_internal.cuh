@@ -5,6 +5,7 @@
 // of it is shared with the CPU oracle.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -71,6 +72,63 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+// ---------------------------------------------------------------------------
+// mbarrier and TMA (tensor copy) wrappers.
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// Makes initialised mbarriers visible to the async (TMA) proxy.
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n\tfence.proxy.async.shared::cta;" ::: "memory");
+}
+// One arrival that also announces `bytes` of incoming transaction data.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// One plain arrival.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Every wait on an mbarrier is bounded: after this long the waiter gives up
+// and reports a fault instead of hanging the GPU.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+// 2-D tensor copy global -> shared of one box at coordinates (x = column,
+// y = row); completes `bar`'s transaction count.  x * 4 must be a multiple
+// of 16 bytes; rows and columns outside the tensor read as zero.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
 // 2^e as a float for -126 <= e <= 127.
 __device__ __forceinline__ float exp2i(int e) { return __uint_as_float(static_cast<uint32_t>(e + 127) << 23); }
 
@@ -96,14 +154,55 @@ __host__ __device__ __forceinline__ void tri_decode(int64_t t, int64_t T, int* b
 }
 
 // ---------------------------------------------------------------------------
+// Tie map of one matrix, read by pass 2 to choose its per-stage inner loop.
+//
+// Pass 2 has a 4-instruction form that is exact unless a one-sided tie
+// d_xy == d_xz (or d_zy == d_zx) occurs; such a tie is two equal entries in
+// one row of D.  The map holds one bit per (pair of 64-blocks {X, Z}, group
+// of 32 consecutive y): set when some row r of X or Z has two equal entries
+// at columns p and q with the block of q being the other side of the pair
+// and p in the y group.  `dirty[b]` marks a block with a row whose repeats
+// were too many to list; every stage of a tile touching it takes the exact
+// loop.  Layout: words[nb][nb][wpp] then dirty[nb], all uint32.
+constexpr int kTieBlock = 64;  // rows / columns per block of the map
+constexpr int kTieGroup = 32;  // y per group of the map
+
+struct TieMapDims {
+  int64_t nb;   // blocks per side, ceil(n / 64)
+  int64_t wpp;  // words per block pair, ceil(ceil(n / 32) / 32)
+};
+
+__host__ __device__ __forceinline__ TieMapDims tie_map_dims(int64_t n) {
+  TieMapDims d;
+  d.nb = (n + kTieBlock - 1) / kTieBlock;
+  d.wpp = ((n + kTieGroup - 1) / kTieGroup + 31) / 32;
+  return d;
+}
+
+// Words of the map including the dirty flags.
+__host__ __device__ __forceinline__ int64_t tie_map_words(int64_t n) {
+  const TieMapDims d = tie_map_dims(n);
+  return d.nb * d.nb * d.wpp + d.nb;
+}
+
+// ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files).
 
 cudaError_t launch_scan(const float* D, int64_t n, ScanResult* out, bool validate, cudaStream_t s);
 cudaError_t launch_focus(const float* D, int64_t n, int32_t* U, const ScanResult* scan, int schedule,
                          cudaStream_t s);
 cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_t s);
-cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, int accum_mode, int schedule,
-                            cudaStream_t s);
+// Clears and fills the tie map (tie_map_words(n) words at `map`).
+cudaError_t launch_tie_map(const float* D, int64_t n, uint32_t* map, cudaStream_t s);
+// `tmap` null: every stage takes the long loop (same result, slower).
+// `scan` is the matrix's scan summary (launch_scan), for the pass-1 scale.
+cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+                            const ScanResult* scan, int accum_mode, int schedule, cudaStream_t s);
+// Reads and clears the device fault word of the pass-2 kernels (nonzero: a
+// bounded wait gave up).  Synchronises `s`.
+cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s);
+// Tensor map of an n x n FP32 row-major matrix with boxes of `rows` x 64.
+cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int rows);
 
 // Batched: descriptors of every matrix, and a flat list of tile work items.
 struct MatrixDesc {

@@ -9,7 +9,9 @@
 // image: every GPU that loads the library holds it (16 MiB + 256 bytes)
 // until the process exits, and matrices are limited to n <= 2048.
 //
-// The kernels are the ones pald_cohesion uses; only the scratch differs.
+// The kernels are the ones pald_cohesion uses; only the scratch differs, and
+// without room for a tie map every stage runs the long form of the inner
+// loop (identical results, slower).
 #include <mutex>
 
 #include "pald_internal.cuh"
@@ -67,11 +69,12 @@ extern "C" pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, i
   float* R = nullptr;
   pald_status st = scratch_address(&R);
   if (st != PALD_OK) return st;
+  // the scan summary (pass-1 scale, and validation when asked) sits after R;
+  // launch_scan clears it before scanning
+  auto* scan = reinterpret_cast<ScanResult*>(R + kNoAllocRFloats);
+  cudaError_t e = launch_scan(D, n, scan, o.validate != 0, s);
+  if (e != cudaSuccess) return cuda_fail(e);
   if (o.validate) {
-    // the summary must start at zero: launch_scan clears it before scanning
-    auto* scan = reinterpret_cast<ScanResult*>(R + kNoAllocRFloats);
-    cudaError_t e = launch_scan(D, n, scan, true, s);
-    if (e != cudaSuccess) return cuda_fail(e);
     ScanResult host{};
     e = cudaMemcpyAsync(&host, scan, sizeof host, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -80,8 +83,10 @@ extern "C" pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, i
   }
   // R is written in full (every entry of the n x n block) before it is read,
   // so nothing left by an earlier call leaks into this one.
-  cudaError_t e = launch_reciprocal(U, R, n, s);
-  if (e == cudaSuccess) e = launch_cohesion(D, R, n, C, o.accum_mode, o.schedule_id, s);
+  e = launch_reciprocal(U, R, n, s);
+  // No tie map (it would need scratch): every stage takes the long form,
+  // which gives the same bits as pald_cohesion's mix of forms.
+  if (e == cudaSuccess) e = launch_cohesion(D, R, n, C, nullptr, scan, o.accum_mode, o.schedule_id, s);
   if (e != cudaSuccess) return cuda_fail(e);
   return PALD_OK;
 }

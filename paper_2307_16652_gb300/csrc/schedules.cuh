@@ -9,7 +9,7 @@
 
 namespace pald {
 
-constexpr int kScheduleCount = 7;
+constexpr int kScheduleCount = 8;
 
 //                       B    H  GX GY CW  BK  unroll
 using FocusS0 = TileGeom<64, 1, 1, 1, 4, 16>;    // 4x4 pairs/thread, 256 threads
@@ -19,6 +19,7 @@ using FocusS3 = TileGeom<128, 2, 2, 1, 4, 16>;   // 8x4 pairs/thread, 128x64 CTA
 using FocusS4 = TileGeom<64, 2, 1, 1, 4, 32>;    // 64x32 CTA tiles, 128 threads
 using FocusS5 = TileGeom<64, 1, 1, 1, 4, 64, 16>;  // 64-deep stages, partly unrolled
 using FocusS6 = TileGeom<128, 2, 2, 1, 4, 32>;   // 8x4 pairs/thread, 32-deep
+using FocusS7 = FocusS2;                         // (schedule 7 is a pass-2 variant)
 
 using CohesionS0 = TileGeom<64, 1, 1, 1, 4, 16>;  // 4x4 pairs/thread, 256 threads
 using CohesionS1 = TileGeom<32, 1, 1, 1, 4, 16>;  // small matrices, 64 threads
@@ -27,6 +28,7 @@ using CohesionS3 = TileGeom<64, 1, 1, 1, 4, 32>;  // deeper stages
 using CohesionS4 = TileGeom<64, 2, 1, 1, 2, 32>;  // 4x2 pairs/thread, deeper stages
 using CohesionS5 = TileGeom<64, 1, 1, 1, 4, 32, 4>;  // 32-deep, loop unrolled by 4 (smaller code)
 using CohesionS6 = TileGeom<64, 1, 1, 1, 4, 64, 8>;  // 64-deep stages, unrolled by 8
+using CohesionS7 = TileGeom<64, 1, 1, 1, 4, 32, 16>;  // S3's tile, TMA-staged, two CTAs per SM
 
 inline int sm_count() {
   int dev = 0, sms = 148;
@@ -42,6 +44,8 @@ inline int sm_count() {
 // the GPU.
 inline int default_focus_schedule(int64_t n) { return n < 1024 ? 1 : 2; }
 
-inline int default_cohesion_schedule(int64_t n) { return n < 1024 ? 1 : (n < 4096 ? 4 : 3); }
+// Schedule 7 (TMA) needs n % 4 == 0 and aligned buffers; otherwise it runs
+// schedule 3's tile with per-thread copies.
+inline int default_cohesion_schedule(int64_t n) { return n < 1024 ? 1 : (n % 4 == 0 ? 7 : (n < 4096 ? 4 : 3)); }
 
 }  // namespace pald

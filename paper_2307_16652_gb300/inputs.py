@@ -238,3 +238,20 @@ def small_tie_heavy(rng: np.random.Generator, n: int, hi: int = 4, dup: bool = F
 def small_points_matrix(rng: np.random.Generator, n: int, dim: int = 3) -> np.ndarray:
     """Tiny Euclidean matrix from standard normal points (ties unlikely)."""
     return euclidean_fp32(rng.standard_normal((n, dim)))
+
+
+def planted_tie_matrix(rng: np.random.Generator, n: int, ties: int, dim: int = 3) -> np.ndarray:
+    """Euclidean FP32 matrix with `ties` planted one-sided ties.
+
+    Each tie copies an entry into another entry of the same row:
+    d_xz = d_zx := d_xy for random distinct x, y, z, so row x holds the same
+    value at columns y and z (the case that decides between pass 2's short
+    and long inner loops).  The matrix stays exactly symmetric with a +0
+    diagonal; it no longer needs to be a metric."""
+    d = small_points_matrix(rng, n, dim=dim)
+    if n < 3:
+        return d
+    for _ in range(ties):
+        x, y, z = rng.choice(n, size=3, replace=False)
+        d[x, z] = d[z, x] = d[x, y]
+    return d

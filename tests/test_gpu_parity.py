@@ -59,7 +59,7 @@ def assert_parity(U, C, Uref, Cref, rtol=C_RTOL):
 
 @pytest.mark.parametrize("n", [2, 3, 4, 5, 17, 31, 33, 64, 65, 127, 129, 130, 200])
 @pytest.mark.parametrize("kind", ["euclid", "tie", "dup"])
-@pytest.mark.parametrize("schedule_id", list(range(7)))
+@pytest.mark.parametrize("schedule_id", list(range(8)))
 def test_ragged_sizes(n, kind, schedule_id):
     rng = np.random.default_rng(n * 7 + schedule_id)
     if kind == "euclid":
