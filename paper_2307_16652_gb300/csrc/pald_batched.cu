@@ -5,9 +5,9 @@
 // upper-triangle tile pairs, and the tiles of all matrices are put in one
 // work list ordered by cost (largest matrices first: a tile's cost is
 // proportional to its matrix order, and longest-first keeps the tail short).
-// The list, the per-matrix descriptors and the per-matrix scan results live in
-// one device allocation owned by a cached plan; the scan, pass-1 and pass-2
-// launches (plus the counter resets) are captured once into a CUDA graph and
+// The list, the per-matrix descriptors, scan results and tie maps live in one
+// device allocation owned by a cached plan; the scan, tie-map, pass-1 and
+// pass-2 launches (plus the resets) are captured once into a CUDA graph and
 // replayed on later calls with the same arguments.
 //
 // Device side: each persistent CTA takes the next work item from a global
@@ -21,6 +21,7 @@
 
 #include "cohesion_core.cuh"
 #include "schedules.cuh"
+#include "tie_map_core.cuh"
 
 namespace pald {
 
@@ -35,30 +36,37 @@ using CG = CohesionS0;  // 64 x 64 super-tiles, one CTA each
 constexpr int kBF = FG::B;
 constexpr int kBC = CG::B;
 constexpr int kScanBlocksPerMatrix = 4;
+constexpr int kTieBlocksPerMatrix = 8;
+constexpr int kRecipBlocksPerMatrix = 8;
+constexpr int kMaxGridY = 65535;  // matrices beyond it are strided over blockIdx.y
 
+// Smallest positive and largest entry of every matrix: matrices along
+// blockIdx.y, each matrix's entries strided over blockIdx.x.
 __global__ void __launch_bounds__(256) batched_scan_kernel(const float* __restrict__ D,
                                                            const MatrixDesc* __restrict__ mats,
-                                                           ScanResult* __restrict__ scans) {
-  const MatrixDesc md = mats[blockIdx.y];
-  const float* M = D + md.off;
-  const int64_t count = static_cast<int64_t>(md.n) * md.n;
-  uint32_t inv_min = 0u, mx = 0u;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
-       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const uint32_t b = __float_as_uint(__ldg(M + i));
-    if (b < 0x7f800000u) {
-      if (b != 0u) inv_min = max(inv_min, ~b);
-      mx = max(mx, b);
+                                                           ScanResult* __restrict__ scans, int count) {
+  for (int m = blockIdx.y; m < count; m += gridDim.y) {
+    const MatrixDesc md = mats[m];
+    const float* M = D + md.off;
+    const int64_t elems = static_cast<int64_t>(md.n) * md.n;
+    uint32_t inv_min = 0u, mx = 0u;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < elems;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      const uint32_t b = __float_as_uint(__ldg(M + i));
+      if (b < 0x7f800000u) {
+        if (b != 0u) inv_min = max(inv_min, ~b);
+        mx = max(mx, b);
+      }
     }
-  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    inv_min = max(inv_min, __shfl_xor_sync(0xffffffffu, inv_min, o));
-    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  }
-  if ((threadIdx.x & 31) == 0) {
-    if (inv_min) atomicMax(&scans[blockIdx.y].inv_min_pos_bits, inv_min);
-    if (mx) atomicMax(&scans[blockIdx.y].max_bits, mx);
+    for (int o = 16; o > 0; o >>= 1) {
+      inv_min = max(inv_min, __shfl_xor_sync(0xffffffffu, inv_min, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      if (inv_min) atomicMax(&scans[m].inv_min_pos_bits, inv_min);
+      if (mx) atomicMax(&scans[m].max_bits, mx);
+    }
   }
 }
 
@@ -86,20 +94,38 @@ __global__ void __launch_bounds__(FG::NT, 2) batched_focus_kernel(const float* _
   }
 }
 
-// R = 1/u for every matrix (zero diagonal): blockIdx.y = matrix.
+// R = 1/u for every matrix (zero diagonal): matrices along blockIdx.y.
 __global__ void __launch_bounds__(256) batched_reciprocal_kernel(const int32_t* __restrict__ U, float* __restrict__ R,
-                                                                 const MatrixDesc* __restrict__ mats) {
-  const MatrixDesc md = mats[blockIdx.y];
-  const bool vec = (md.n % 4) == 0;  // offsets are multiples of 4 elements
-  for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x) reciprocal_rows(U + md.off, R + md.off, md.n, row, vec);
+                                                                 const MatrixDesc* __restrict__ mats, int count) {
+  for (int m = blockIdx.y; m < count; m += gridDim.y) {
+    const MatrixDesc md = mats[m];
+    const bool vec = (md.n % 4) == 0;  // offsets are multiples of 4 elements
+    for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x)
+      reciprocal_rows(U + md.off, R + md.off, md.n, row, vec);
+  }
+}
+
+// Tie maps of every matrix (zeroed before): matrices along blockIdx.y, rows
+// strided over blockIdx.x, one CTA per row at a time.
+__global__ void __launch_bounds__(TieSmall::kThreads) batched_tie_kernel(const float* __restrict__ D,
+                                                                         const MatrixDesc* __restrict__ mats,
+                                                                         uint32_t* __restrict__ tmaps, int count) {
+  __shared__ TieSmall::Smem sm;
+  for (int m = blockIdx.y; m < count; m += gridDim.y) {
+    const MatrixDesc md = mats[m];
+    const TieMapDims dm = tie_map_dims(md.n);
+    for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x)
+      tie_map_row<TieSmall>(D + md.off, md.n, row, tmaps + md.tmap_off, dm, sm);
+  }
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(CG::NT) batched_cohesion_kernel(const float* __restrict__ D,
-                                                                  const float* __restrict__ R,
-                                                                  float* __restrict__ C,
-                                                                  const MatrixDesc* __restrict__ mats,
-                                                                  const ScanResult* __restrict__ scans,
+__global__ void __launch_bounds__(CG::NT, 2) batched_cohesion_kernel(const float* __restrict__ D,
+                                                                     const float* __restrict__ R,
+                                                                     float* __restrict__ C,
+                                                                     const MatrixDesc* __restrict__ mats,
+                                                                     const ScanResult* __restrict__ scans,
+                                                                     const uint32_t* __restrict__ tmaps,
                                                                   const WorkItem* __restrict__ items,
                                                                   int64_t n_items, int* counter) {
   extern __shared__ __align__(16) float smem[];
@@ -110,7 +136,8 @@ __global__ void __launch_bounds__(CG::NT) batched_cohesion_kernel(const float* _
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
     const float S = focus_scale(scans[w.matrix].inv_min_pos_bits);
-    cohesion_tile<CG, MODE>(D + md.off, R + md.off, md.n, C + md.off, nullptr, S, w.bi, w.bj, w.slice, smem);
+    cohesion_tile<CG, MODE>(D + md.off, R + md.off, md.n, C + md.off, tmaps + md.tmap_off, S, w.bi, w.bj, w.slice,
+                            smem);
   }
 }
 
@@ -168,10 +195,12 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   // descriptors and tile lists
   std::vector<MatrixDesc> mats(count);
   std::vector<int> order(count);
+  int64_t tmap_words = 0;
   for (int i = 0; i < count; ++i) {
     const int64_t Tf = (ns[i] + kBF - 1) / kBF, Tc = (ns[i] + kBC - 1) / kBC;
     mats[i] = MatrixDesc{offs[i], static_cast<int32_t>(ns[i]), static_cast<int32_t>(Tf * (Tf + 1) / 2),
-                         static_cast<int32_t>(Tc * (Tc + 1) / 2), 0};
+                         static_cast<int32_t>(Tc * (Tc + 1) / 2), 0, tmap_words};
+    tmap_words += tie_map_words(ns[i]);
     order[i] = i;
   }
   // longest-processing-time first: a tile costs ~ n (its streamed dimension)
@@ -193,7 +222,8 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   const size_t o_counters = align_up(o_citems + sizeof(WorkItem) * citems.size(), 256);
   int64_t r_elems = 0;  // R uses the same offsets as D, U and C
   for (int i = 0; i < count; ++i) r_elems = std::max<int64_t>(r_elems, offs[i] + ns[i] * ns[i]);
-  const size_t o_recip = align_up(o_counters + 256, 256);
+  const size_t o_tmaps = align_up(o_counters + 256, 256);
+  const size_t o_recip = align_up(o_tmaps + sizeof(uint32_t) * static_cast<size_t>(tmap_words), 256);
   const size_t total = o_recip + sizeof(float) * static_cast<size_t>(r_elems);
 
   Plan p;
@@ -206,6 +236,7 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   auto* d_fitems = reinterpret_cast<WorkItem*>(base + o_fitems);
   auto* d_citems = reinterpret_cast<WorkItem*>(base + o_citems);
   auto* d_counters = reinterpret_cast<int*>(base + o_counters);
+  auto* d_tmaps = reinterpret_cast<uint32_t*>(base + o_tmaps);
   auto* d_recip = reinterpret_cast<float*>(base + o_recip);
   e = cudaMemcpy(d_mats, mats.data(), sizeof(MatrixDesc) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_fitems, fitems.data(), sizeof(WorkItem) * fitems.size(), cudaMemcpyHostToDevice);
@@ -237,18 +268,21 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
 
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
+    const unsigned gy = static_cast<unsigned>(std::min(count, kMaxGridY));
     cudaMemsetAsync(d_scans, 0, sizeof(ScanResult) * count, cs);
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), cs);
-    batched_scan_kernel<<<dim3(kScanBlocksPerMatrix, count), 256, 0, cs>>>(D, d_mats, d_scans);
+    cudaMemsetAsync(d_tmaps, 0, sizeof(uint32_t) * static_cast<size_t>(tmap_words), cs);
+    batched_scan_kernel<<<dim3(kScanBlocksPerMatrix, gy), 256, 0, cs>>>(D, d_mats, d_scans, count);
+    batched_tie_kernel<<<dim3(kTieBlocksPerMatrix, gy), TieSmall::kThreads, 0, cs>>>(D, d_mats, d_tmaps, count);
     batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_mats, d_scans, d_fitems,
                                                 static_cast<int64_t>(fitems.size()), d_counters);
-    batched_reciprocal_kernel<<<dim3(8, count), 256, 0, cs>>>(U, d_recip, d_mats);
+    batched_reciprocal_kernel<<<dim3(kRecipBlocksPerMatrix, gy), 256, 0, cs>>>(U, d_recip, d_mats, count);
     if (plain)
       batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, csmem, cs>>>(
-          D, d_recip, C, d_mats, d_scans, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
+          D, d_recip, C, d_mats, d_scans, d_tmaps, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
     else
       batched_cohesion_kernel<PALD_ACCUM_COMPENSATED><<<gc, CG::NT, csmem, cs>>>(
-          D, d_recip, C, d_mats, d_scans, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
+          D, d_recip, C, d_mats, d_scans, d_tmaps, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
     cudaError_t launch_err = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &p.graph);
     if (e == cudaSuccess && launch_err != cudaSuccess) e = launch_err;

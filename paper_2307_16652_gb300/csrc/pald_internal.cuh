@@ -211,6 +211,7 @@ struct MatrixDesc {
   int32_t tiles_focus;     // number of upper-triangle tiles of the pass-1 schedule
   int32_t tiles_cohesion;  // same for pass 2
   int32_t pad;
+  int64_t tmap_off;        // word offset of the matrix's tie map
 };
 struct WorkItem {
   int32_t matrix;

@@ -1,6 +1,6 @@
 // Tie map of one matrix (see tie_map_core.cuh): one CTA per row, strided
 // over the rows, one CTA per SM (the hash table takes 147 KB of shared
-// memory).
+// memory).  The batched path has its own smaller configuration.
 #include "schedules.cuh"
 #include "tie_map_core.cuh"
 
@@ -8,11 +8,11 @@ namespace pald {
 
 namespace {
 
-__global__ void __launch_bounds__(kTieThreads, 1)
+__global__ void __launch_bounds__(TieLarge::kThreads, 1)
     tie_map_kernel(const float* __restrict__ D, int64_t n, uint32_t* __restrict__ map, TieMapDims dm) {
   extern __shared__ __align__(16) unsigned char tie_smem[];
-  TieSmem& sm = *reinterpret_cast<TieSmem*>(tie_smem);
-  for (int64_t row = blockIdx.x; row < n; row += gridDim.x) tie_map_row(D, n, row, map, dm, sm);
+  auto& sm = *reinterpret_cast<TieLarge::Smem*>(tie_smem);
+  for (int64_t row = blockIdx.x; row < n; row += gridDim.x) tie_map_row<TieLarge>(D, n, row, map, dm, sm);
 }
 
 }  // namespace
@@ -24,13 +24,13 @@ cudaError_t launch_tie_map(const float* D, int64_t n, uint32_t* map, cudaStream_
   static bool attr_set = false;  // idempotent: racing setters write the same value
   if (!attr_set) {
     e = cudaFuncSetAttribute(tie_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sizeof(TieSmem)));
+                             static_cast<int>(sizeof(TieLarge::Smem)));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int64_t cap = sm_count();
   const int64_t grid = n < cap ? n : cap;
-  tie_map_kernel<<<static_cast<unsigned>(grid), kTieThreads, sizeof(TieSmem), s>>>(D, n, map, dm);
+  tie_map_kernel<<<static_cast<unsigned>(grid), TieLarge::kThreads, sizeof(TieLarge::Smem), s>>>(D, n, map, dm);
   return cudaGetLastError();
 }
 

@@ -18,31 +18,40 @@
 // (open addressing, linear probing); an insert that finds its value already
 // present is a repeat and is listed with its slot.  After a barrier, each
 // listed repeat marks its pairs with the slot's first column and with every
-// other repeat of the same slot.  Rows longer than kTiePart are processed in
-// ceil(n / kTiePart) passes, each taking the values whose hash falls in its
-// share, so the table never fills beyond one half.  A row with more than
-// kTieDupCap repeats in one pass (e.g. small-integer distances) is not
-// listed: its block is flagged dirty instead.
+// other repeat of the same slot.  Rows longer than half the table are processed in
+// ceil(n / (slots / 2)) passes, each taking the values whose hash falls in
+// its share, so the table never fills beyond one half.  A row with more than
+// DUPCAP repeats in one pass (e.g. small-integer distances) is not listed:
+// its block is flagged dirty instead.
 #pragma once
 
 #include "pald_internal.cuh"
 
 namespace pald {
 
-constexpr int kTieThreads = 1024;
-constexpr int kTieSlots = 16384;   // hash slots (power of two)
-constexpr int kTiePart = 8192;     // values per pass: load factor <= 1/2
-constexpr int kTieDupCap = 2048;   // listed repeats per pass
 constexpr uint32_t kTieEmpty = 0xffffffffu;  // a NaN pattern: never a valid entry
 
-struct TieSmem {
-  uint32_t key[kTieSlots];    // value bits
-  int32_t first[kTieSlots];   // column of the first occurrence
-  int32_t dslot[kTieDupCap];  // repeats: slot ...
-  int32_t dcol[kTieDupCap];   // ... and column
-  int32_t ndup;
-  int32_t overflow;
+// Shared-memory sizes of one row's scan: THREADS threads, a table of SLOTS
+// hash slots (a power of two; each pass takes at most SLOTS / 2 values) and
+// room to list DUPCAP repeated values per pass.
+template <int THREADS, int SLOTS, int DUPCAP>
+struct TieConfig {
+  static constexpr int kThreads = THREADS;
+  static constexpr int kSlots = SLOTS;
+  static constexpr int kPart = SLOTS / 2;
+  static constexpr int kDupCap = DUPCAP;
+  static_assert((SLOTS & (SLOTS - 1)) == 0, "hash slots must be a power of two");
+  struct Smem {
+    uint32_t key[SLOTS];    // value bits
+    int32_t first[SLOTS];   // column of the first occurrence
+    int32_t dslot[DUPCAP];  // repeats: slot ...
+    int32_t dcol[DUPCAP];   // ... and column
+    int32_t ndup;
+    int32_t overflow;
+  };
 };
+using TieLarge = TieConfig<1024, 16384, 2048>;  // one matrix, any order: 147 KB, one CTA per SM
+using TieSmall = TieConfig<256, 2048, 512>;     // batched orders <= 4096: 20 KB, many CTAs per SM
 
 // 32-bit finalizer of MurmurHash3 (Appleby, public domain): mixes all input
 // bits into all output bits, so the table slot and the pass share are
@@ -68,30 +77,32 @@ __device__ __forceinline__ void tie_mark(uint32_t* map, const TieMapDims& dm, in
   atomicOr(map + (a * dm.nb + b) * dm.wpp + (g >> 5), 1u << (g & 31));
 }
 
-// All kTieThreads threads of the CTA process row `row` of the n x n matrix
+// All Cfg::kThreads threads of the CTA process row `row` of the n x n matrix
 // at `Dm` into `map` (already zeroed).  Contains barriers: call uniformly.
+template <class Cfg>
 __device__ __forceinline__ void tie_map_row(const float* __restrict__ Dm, int64_t n, int64_t row, uint32_t* map,
-                                            const TieMapDims& dm, TieSmem& sm) {
+                                            const TieMapDims& dm, typename Cfg::Smem& sm) {
+  constexpr int NT = Cfg::kThreads, SLOTS = Cfg::kSlots, CAP = Cfg::kDupCap;
   const float* drow = Dm + row * n;
   const int64_t brow = row / kTieBlock;
-  const int parts = static_cast<int>((n + kTiePart - 1) / kTiePart);
+  const int parts = static_cast<int>((n + Cfg::kPart - 1) / Cfg::kPart);
   bool dirty = false;
   for (int part = 0; part < parts && !dirty; ++part) {
-    for (int i = threadIdx.x; i < kTieSlots; i += kTieThreads) sm.key[i] = kTieEmpty;
+    for (int i = threadIdx.x; i < SLOTS; i += NT) sm.key[i] = kTieEmpty;
     if (threadIdx.x == 0) {
       sm.ndup = 0;
       sm.overflow = 0;
     }
     __syncthreads();
-    for (int64_t c = threadIdx.x; c < n; c += kTieThreads) {
+    for (int64_t c = threadIdx.x; c < n; c += NT) {
       // +0.0f turns a stray -0.0 into +0.0 (equal under comparison)
       const uint32_t v = __float_as_uint(__fadd_rn(__ldg(drow + c), 0.0f));
       const uint32_t h = tie_hash(v);
       if (parts > 1 && static_cast<int>((static_cast<uint64_t>(h) * static_cast<uint64_t>(parts)) >> 32) != part)
         continue;
-      uint32_t slot = h & (kTieSlots - 1);
+      uint32_t slot = h & (SLOTS - 1);
       int k = 0;
-      for (; k < kTieSlots; ++k) {
+      for (; k < SLOTS; ++k) {
         const uint32_t old = atomicCAS(&sm.key[slot], kTieEmpty, v);
         if (old == kTieEmpty) {
           sm.first[slot] = static_cast<int32_t>(c);
@@ -99,21 +110,21 @@ __device__ __forceinline__ void tie_map_row(const float* __restrict__ Dm, int64_
         }
         if (old == v) {
           const int i = atomicAdd(&sm.ndup, 1);
-          if (i < kTieDupCap) {
+          if (i < CAP) {
             sm.dslot[i] = static_cast<int32_t>(slot);
             sm.dcol[i] = static_cast<int32_t>(c);
           }
           break;
         }
-        slot = (slot + 1) & (kTieSlots - 1);
+        slot = (slot + 1) & (SLOTS - 1);
       }
-      if (k == kTieSlots) sm.overflow = 1;  // only for values outside the input contract
+      if (k == SLOTS) sm.overflow = 1;  // only for values outside the input contract
     }
     __syncthreads();
     const int nd = sm.ndup;
-    dirty = nd > kTieDupCap || sm.overflow != 0;
+    dirty = nd > CAP || sm.overflow != 0;
     if (!dirty) {
-      for (int i = threadIdx.x; i < nd; i += kTieThreads) {
+      for (int i = threadIdx.x; i < nd; i += NT) {
         const int s = sm.dslot[i];
         const int64_t ci = sm.dcol[i];
         const int64_t f = sm.first[s];

@@ -108,3 +108,30 @@ def test_batched_against_oracle_and_single_path():
         worst = max(worst, mx)
     print(f"batched: {len(pick)} matrices vs oracle, max rel {worst:.3e}")
     binding.pald_release()
+
+
+def test_batched_more_matrices_than_one_grid_dimension():
+    # 70000 tiny matrices: more than a launch's y dimension holds, so the
+    # per-matrix kernels stride over the grid; every matrix checked exactly
+    rng = np.random.default_rng(7)
+    count = 70000
+    ns = rng.integers(2, 6, size=count).astype(np.int64)
+    offs, total = inputs.packed_offsets(ns)
+    Dh = np.zeros(total, np.float32)
+    mats = []
+    for i in range(count):
+        n = int(ns[i])
+        Di = inputs.small_tie_heavy(rng, n, hi=3) if i % 2 else inputs.small_points_matrix(rng, n, dim=2)
+        Dh[offs[i]:offs[i] + n * n] = Di.ravel()
+        mats.append(Di)
+    D = torch.from_numpy(Dh).cuda()
+    U = torch.zeros(total, dtype=torch.int32, device="cuda")
+    C = torch.zeros(total, dtype=torch.float32, device="cuda")
+    binding.pald_batched(ns, offs, D, U, C)
+    torch.cuda.synchronize()
+    Uh, Ch = U.cpu().numpy(), C.cpu().numpy()
+    for i in list(range(0, count, 997)) + [count - 1]:
+        n = int(ns[i])
+        Ur, Cr = oracle.focus_and_cohesion(mats[i])
+        check_rows(Uh[offs[i]:offs[i] + n * n].reshape(n, n), Ch[offs[i]:offs[i] + n * n].reshape(n, n), Ur, Cr)
+    binding.pald_release()
