@@ -344,56 +344,41 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
 }
 
 // ---------------------------------------------------------------------------
-// TMA-staged tile.  One thread issues four tensor copies per stage (the D and
-// R panels of X and Z, each BK rows x 64 columns, zero-filled outside the
-// matrix) that complete on the buffer's mbarrier; every thread waits on it
-// with a time limit.  One CTA barrier per stage keeps all warps on the same
-// stage, hence on the same (short or long) loop body, which matters for the
-// instruction cache.  No per-thread copy arithmetic remains in the loop, and
-// the kernel fits two CTAs per SM (four warps per scheduler).  Requires
-// 64 x 64 tiles, n % 4 == 0 and 16-byte aligned D and R (the TMA row pitch).
+// TMA-staged tile (64 x 64, see tma_ring.cuh): the D and R panels of X and Z
+// come from the tensor maps tmD and tmR of the n x n matrices (which may be
+// row-padded copies); the per-pair constants are read from D (row pitch n)
+// and C is written with row pitch n.  No per-thread copy arithmetic remains
+// in the loop, and the kernel fits two CTAs per SM (four warps per
+// scheduler).
 
-constexpr int kTmaStages = 3;
 constexpr int kTieWordsMax = 1024;  // tie-map words of one block pair for n <= 2^20
 
 template <class Geo>
 struct CohesionTmaSmem {
-  static constexpr int PANEL = Geo::BK * 64;  // floats of one panel stage
-  static constexpr int FLOATS = kTmaStages * 4 * PANEL;
-  // panels, mbarriers, the tile's tie-map words, alignment slack
-  static constexpr int bytes(int64_t n) {
-    return FLOATS * 4 + 8 * kTmaStages + 4 * static_cast<int>(tie_map_dims(n).wpp) + 128;
-  }
-  static constexpr int MAX_BYTES = FLOATS * 4 + 8 * kTmaStages + 4 * kTieWordsMax + 128;
+  using Ring = TmaRing<4, Geo::BK>;
+  // ring (128-byte aligned), then the tile's tie-map words
+  static constexpr int bytes(int64_t n) { return Ring::BYTES + 128 + 4 * static_cast<int>(tie_map_dims(n).wpp); }
+  static constexpr int MAX_BYTES = Ring::BYTES + 128 + 4 * kTieWordsMax;
 };
 
-// Returns false (and the caller records a fault) when a wait ran out of
-// time; the CTA then stops early and its outputs are unspecified.
+// Returns false when a wait ran out of time; the CTA then stops early and
+// its outputs are unspecified.  `tie_words` holds tie_map_dims(n).wpp words
+// of shared memory.
 template <class Geo, int MODE>
-__device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const CUtensorMap* tmR, int64_t n,
-                                                  float* __restrict__ C, const float* __restrict__ D,
+__device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const CUtensorMap* tmR,
+                                                  const float* __restrict__ D, int64_t n, float* __restrict__ C,
                                                   const uint32_t* __restrict__ tmap, float S, int bi, int bj,
-                                                  float* smem_raw) {
+                                                  bool vec, TmaRing<4, Geo::BK>& ring, uint32_t* tie_words) {
   constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY, NT = Geo::NT;
-  constexpr int PANEL = CohesionTmaSmem<Geo>::PANEL;
-  static_assert(Geo::BX == 64 && Geo::BY == 64, "TMA tiles are 64 x 64");
+  static_assert(Geo::BX == 64 && Geo::BY == 64 && Geo::TPX == 16 && Geo::TPY == 16 && Geo::GX == 1 &&
+                    Geo::GY == 1 && Geo::CW == 4,
+                "TMA tiles are 64 x 64 with 4 x 4 pairs per thread");
   cohesion_tile_checks<Geo>();
-  const int tx = threadIdx.x % Geo::TPX, tz = threadIdx.x / Geo::TPX;
+  int tx, tz;
+  const bool active = tile_block_64(bi, bj, n, threadIdx.x, &tx, &tz);
   const int nstages = static_cast<int>((n + BK - 1) / BK);
 
-  // 128-byte aligned panels, the mbarriers, the tie words (offsets from the
-  // shared array itself, so the compiler keeps shared-memory loads)
-  const int pad = static_cast<int>((128u - (smem_u32(smem_raw) & 127u)) & 127u) / 4;
-  float* panels = smem_raw + pad;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(panels + CohesionTmaSmem<Geo>::FLOATS);
-  uint32_t* tie_words = reinterpret_cast<uint32_t*>(bars + kTmaStages);
-  auto panel = [&](int buf, int k) { return panels + (buf * 4 + k) * PANEL; };  // k: Ad, Ar, Bd, Br
-
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int b = 0; b < kTmaStages; ++b) mbar_init(smem_u32(bars + b), 1);
-    mbar_fence_init();
-  }
+  if (threadIdx.x == 0) ring.init();
   // the tile's tie-map row (all ones when there is no map or a block is dirty)
   {
     const TieMapDims dm = tie_map_dims(n);
@@ -404,64 +389,43 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
     for (int w = threadIdx.x; w < dm.wpp; w += NT) tie_words[w] = all_long ? ~0u : __ldg(row + w);
   }
   __syncthreads();
-  auto issue = [&](int q) {  // stage q into buffer q % kTmaStages (one thread)
-    const int buf = q % kTmaStages;
-    const uint32_t bar = smem_u32(bars + buf);
-    const int y0 = q * BK;
-    mbar_expect_tx(bar, 4u * PANEL * sizeof(float));
-    tma_load_2d(smem_u32(panel(buf, 0)), tmD, bi * 64, y0, bar);
-    tma_load_2d(smem_u32(panel(buf, 1)), tmR, bi * 64, y0, bar);
-    tma_load_2d(smem_u32(panel(buf, 2)), tmD, bj * 64, y0, bar);
-    tma_load_2d(smem_u32(panel(buf, 3)), tmR, bj * 64, y0, bar);
-  };
-  if (threadIdx.x == 0)
-    for (int q = 0; q < kTmaStages - 1 && q < nstages; ++q) issue(q);
 
   float cv[TX][TY];
   uint64_t sacc[TX][TY], hacc[TX][TY];
   cohesion_init<Geo>(D, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, tz, S, cv, sacc, hacc);
 
   constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
-  int st = 0;
-  bool aborted = false;
-  for (; st < nstages; ++st) {
-    const int buf = st % kTmaStages;
-    const bool ok = mbar_wait_bounded(smem_u32(bars + buf), static_cast<uint32_t>((st / kTmaStages) & 1));
-    // one barrier per stage: stage st has landed for every thread (or some
-    // thread gave up), and every thread is done with stage st-1's buffer
-    if (__syncthreads_or(!ok)) {
-      aborted = true;
-      break;
-    }
-    if (threadIdx.x == 0 && st + kTmaStages - 1 < nstages) issue(st + kTmaStages - 1);
-    const int g = st * BK / kTieGroup;
-    if ((tie_words[g >> 5] >> (g & 31)) & kGroupMask)
-      cohesion_stage<Geo, MODE, false>(panel(buf, 0), panel(buf, 1), panel(buf, 2), panel(buf, 3), tx, tz, S, cv,
-                                       sacc, hacc);
-    else
-      cohesion_stage<Geo, MODE, true>(panel(buf, 0), panel(buf, 1), panel(buf, 2), panel(buf, 3), tx, tz, S, cv,
-                                      sacc, hacc);
-  }
-  if (aborted) {
-    // let the copies already issued (stages st .. st+kTmaStages-2) land
-    // before the CTA's shared memory is released, each wait again bounded
-    if (threadIdx.x == 0) {
-      for (int q = st; q < st + kTmaStages - 1 && q < nstages; ++q)
-        mbar_wait_bounded(smem_u32(bars + q % kTmaStages), static_cast<uint32_t>((q / kTmaStages) & 1));
-    }
-    __syncthreads();
-    return false;
-  }
-  cohesion_finish<Geo, MODE>(C, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, tz, bi != bj, true, sacc, hacc);
-  return true;
+  const CUtensorMap* const maps[4] = {tmD, tmR, tmD, tmR};
+  const int cols[4] = {bi * 64, bi * 64, bj * 64, bj * 64};
+  const bool ok = tma_pipeline(
+      ring, nstages, [&](int q) { ring.issue(q, maps, cols); },
+      [&](int st, int buf) {
+        if (!active) return;
+        const int g = st * BK / kTieGroup;
+        if ((tie_words[g >> 5] >> (g & 31)) & kGroupMask)
+          cohesion_stage<Geo, MODE, false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
+                                           ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc);
+        else
+          cohesion_stage<Geo, MODE, true>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
+                                          ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc);
+      });
+  __syncthreads();
+  if (threadIdx.x == 0) ring.inval();
+  // off the diagonal, or for an above-diagonal block of a diagonal tile,
+  // the block's mirror (the zx lanes) is written too
+  if (ok && active)
+    cohesion_finish<Geo, MODE>(C, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, tz, tx != tz || bi != bj, vec, sacc,
+                               hacc);
+  return ok;
 }
 
 // R[row][col] = 1/u (correctly rounded FP32), 0 on the diagonal and where
-// u <= 0; rows [r0, r1) of one n x n matrix, one warp per row stretch.
-__device__ __forceinline__ void reciprocal_rows(const int32_t* __restrict__ U, float* __restrict__ R, int64_t n,
-                                                int64_t row, bool vec) {
+// u <= 0, for one row of an n x n matrix; U has row pitch n, R row pitch
+// `rp` (a multiple of 4 when `vec`).  The CTA's threads share the row.
+__device__ __forceinline__ void reciprocal_rows(const int32_t* __restrict__ U, int64_t n, float* __restrict__ R,
+                                                int64_t rp, int64_t row, bool vec) {
   const int32_t* u = U + row * n;
-  float* r = R + row * n;
+  float* r = R + row * rp;
   if (vec) {
     const int64_t n4 = n / 4;
     for (int64_t k = threadIdx.x; k < n4; k += blockDim.x) {

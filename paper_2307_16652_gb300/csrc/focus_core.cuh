@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "tile_geom.cuh"
+#include "tma_ring.cuh"
 
 namespace pald {
 
@@ -139,9 +140,124 @@ struct FocusSmem {
   static constexpr int FLOATS = kPipe * (Geo::SX + Geo::SY);  // kPipe stages of both operands
 };
 
+// Thresholds c = -d_xy * scale (exact: power-of-two scaling) and zeroed counts.
+template <class Geo>
+__device__ __forceinline__ void focus_init(const float* __restrict__ D, int64_t n, int64_t X0, int64_t Y0, int tx,
+                                           int ty, float scale, float (&cst)[Geo::TX][Geo::TY],
+                                           uint64_t (&acc)[Geo::TX][Geo::TY]) {
+#pragma unroll
+  for (int i = 0; i < Geo::TX; ++i) {
+    const int64_t x = X0 + Geo::row_off(tx, i);
+#pragma unroll
+    for (int j = 0; j < Geo::TY; ++j) {
+      const int64_t y = Y0 + Geo::col_off(ty, j);
+      cst[i][j] = (x < n && y < n) ? -__ldg(D + x * n + y) * scale : 0.f;
+      acc[i][j] = 0ull;
+    }
+  }
+}
+
+// One pipeline stage (BK consecutive z): as = D[z-stage][X], bs = D[z-stage][Y].
+template <class Geo>
+__device__ __forceinline__ void focus_stage(const float* as, const float* bs, int tx, int ty, float scale,
+                                            const float (&cst)[Geo::TX][Geo::TY],
+                                            uint64_t (&acc)[Geo::TX][Geo::TY]) {
+  constexpr int TX = Geo::TX, TY = Geo::TY;
+#pragma unroll Geo::UNR / 2
+  for (int kk = 0; kk < Geo::BK; kk += 2) {
+    float a0[TX], b0[TY], a1[TX], b1[TY];
+#pragma unroll
+    for (int g = 0; g < Geo::GX; ++g) {
+      lds<4>(as + kk * Geo::BX + Geo::row_off(tx, 4 * g), a0 + 4 * g);
+      lds<4>(as + (kk + 1) * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
+    }
+#pragma unroll
+    for (int g = 0; g < Geo::GY; ++g) {
+      lds<Geo::CW>(bs + kk * Geo::BY + Geo::col_off(ty, Geo::CW * g), b0 + Geo::CW * g);
+      lds<Geo::CW>(bs + (kk + 1) * Geo::BY + Geo::col_off(ty, Geo::CW * g), b1 + Geo::CW * g);
+    }
+#pragma unroll
+    for (int i = 0; i < TX; ++i)
+#pragma unroll
+      for (int j = 0; j < TY; ++j) focus_step2(acc[i][j], a0[i], b0[j], a1[i], b1[j], scale, cst[i][j]);
+  }
+}
+
+// 1/u as pass 2 reads it: correctly rounded, 0 on the diagonal (which
+// removes the y == x term) and for u <= 0.
+__device__ __forceinline__ float recip_entry(int32_t u, int64_t row, int64_t col) {
+  return (u <= 0 || row == col) ? 0.f : __frcp_rn(static_cast<float>(u));
+}
+
+// Stores W consecutive values of row `row` at column `col` of a matrix of
+// order n stored with row pitch `pitch`.
+template <int W>
+__device__ __forceinline__ void storew_pitched(float* __restrict__ M, int64_t n, int64_t pitch, int64_t row,
+                                               int64_t col, const float* v, bool vec) {
+  if (row >= n) return;
+  float* p = M + row * pitch + col;
+  if (W == 4 && vec && col + 3 < n) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    return;
+  }
+#pragma unroll
+  for (int k = 0; k < W; ++k)
+    if (col + k < n) p[k] = v[k];
+}
+
+// u = n - #{z : min > t} (zero-filled z beyond n never count: m = 0 <= t);
+// stores U[X, Y] and, when `mirror`, U[Y, X].  U has row pitch n.  With a
+// non-null R it also stores R = 1/u (recip_entry) there, row pitch `rpitch`
+// (a multiple of 4), so that pass 2 needs no reciprocal kernel.
+template <class Geo>
+__device__ __forceinline__ void focus_finish(int32_t* __restrict__ U, int64_t n, int64_t X0, int64_t Y0, int tx,
+                                             int ty, bool mirror, bool vec, const uint64_t (&acc)[Geo::TX][Geo::TY],
+                                             float* __restrict__ R = nullptr, int64_t rpitch = 0) {
+  const int nn = static_cast<int>(n);
+#pragma unroll
+  for (int i = 0; i < Geo::TX; ++i) {
+    const int64_t x = X0 + Geo::row_off(tx, i);
+#pragma unroll
+    for (int gj = 0; gj < Geo::GY; ++gj) {
+      const int64_t y0 = Y0 + Geo::col_off(ty, Geo::CW * gj);
+      int32_t v[Geo::CW];
+#pragma unroll
+      for (int k = 0; k < Geo::CW; ++k) v[k] = nn - count_of(acc[i][Geo::CW * gj + k]);
+      storew<Geo::CW>(U, n, x, y0, v, vec);
+      if (R) {
+        float r[Geo::CW];
+#pragma unroll
+        for (int k = 0; k < Geo::CW; ++k) r[k] = recip_entry(v[k], x, y0 + k);
+        storew_pitched<Geo::CW>(R, n, rpitch, x, y0, r, true);
+      }
+    }
+  }
+  if (mirror) {
+#pragma unroll
+    for (int j = 0; j < Geo::TY; ++j) {
+      const int64_t y = Y0 + Geo::col_off(ty, j);
+#pragma unroll
+      for (int gi = 0; gi < Geo::GX; ++gi) {
+        const int64_t x0 = X0 + Geo::row_off(tx, 4 * gi);
+        int32_t v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = nn - count_of(acc[4 * gi + k][j]);
+        storew<4>(U, n, y, x0, v, vec);
+        if (R) {
+          float r[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) r[k] = recip_entry(v[k], y, x0 + k);
+          storew_pitched<4>(R, n, rpitch, y, x0, r, true);
+        }
+      }
+    }
+  }
+}
+
 // Computes and stores U[X, Y] (and U[Y, X] off the diagonal) for super-tile
-// (bi, bj), column slice `slice`.  `smem` holds FocusSmem<Geo>::FLOATS
-// floats.  Must be called by all Geo::NT threads.
+// (bi, bj), column slice `slice`, staging operands with per-thread cp.async
+// copies.  `smem` holds FocusSmem<Geo>::FLOATS floats.  Must be called by
+// all Geo::NT threads.
 template <class Geo>
 __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t n, int32_t* __restrict__ U, int bi,
                                            int bj, int slice, float scale, float* smem) {
@@ -163,23 +279,9 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
     }
     cp_async_commit();
   }
-
-  // thresholds t = d_xy -> c = -t * scale (exact: power-of-two scaling)
   float cst[TX][TY];
   uint64_t acc[TX][TY];
-#pragma unroll
-  for (int i = 0; i < TX; ++i) {
-    const int64_t x = X0 + Geo::row_off(tx, i);
-#pragma unroll
-    for (int j = 0; j < TY; ++j) {
-      const int64_t y = Y0 + Geo::col_off(ty, j);
-      cst[i][j] = (x < n && y < n) ? -__ldg(D + x * n + y) * scale : 0.f;
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < TX; ++i)
-#pragma unroll
-    for (int j = 0; j < TY; ++j) acc[i][j] = 0ull;
+  focus_init<Geo>(D, n, X0, Y0, tx, ty, scale, cst, acc);
 
   for (int64_t st = 0; st < nstages; ++st) {
     const int buf = static_cast<int>(st % kPipe);
@@ -191,54 +293,47 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
       stage_rows<Geo::BY, NT, BK>(Bs + nb * Geo::SY, D, n, (st + kPipe - 1) * BK, Y0, vec);
     }
     cp_async_commit();  // possibly empty: keeps one group per stage
-    const float* as = As + buf * Geo::SX;
-    const float* bs = Bs + buf * Geo::SY;
-#pragma unroll Geo::UNR / 2
-    for (int kk = 0; kk < BK; kk += 2) {
-      float a0[TX], b0[TY], a1[TX], b1[TY];
-#pragma unroll
-      for (int g = 0; g < Geo::GX; ++g) {
-        lds<4>(as + kk * Geo::BX + Geo::row_off(tx, 4 * g), a0 + 4 * g);
-        lds<4>(as + (kk + 1) * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
-      }
-#pragma unroll
-      for (int g = 0; g < Geo::GY; ++g) {
-        lds<Geo::CW>(bs + kk * Geo::BY + Geo::col_off(ty, Geo::CW * g), b0 + Geo::CW * g);
-        lds<Geo::CW>(bs + (kk + 1) * Geo::BY + Geo::col_off(ty, Geo::CW * g), b1 + Geo::CW * g);
-      }
-#pragma unroll
-      for (int i = 0; i < TX; ++i)
-#pragma unroll
-        for (int j = 0; j < TY; ++j) focus_step2(acc[i][j], a0[i], b0[j], a1[i], b1[j], scale, cst[i][j]);
-    }
+    focus_stage<Geo>(As + buf * Geo::SX, Bs + buf * Geo::SY, tx, ty, scale, cst, acc);
   }
+  focus_finish<Geo>(U, n, X0, Y0, tx, ty, bi != bj, vec, acc);
+}
 
-  // u = n - #{z : min > t}; zero-filled z beyond n never count (m = 0 <= t)
-  const int nn = static_cast<int>(n);
-#pragma unroll
-  for (int i = 0; i < TX; ++i) {
-    const int64_t x = X0 + Geo::row_off(tx, i);
-#pragma unroll
-    for (int gj = 0; gj < Geo::GY; ++gj) {
-      int32_t v[Geo::CW];
-#pragma unroll
-      for (int k = 0; k < Geo::CW; ++k) v[k] = nn - count_of(acc[i][Geo::CW * gj + k]);
-      storew<Geo::CW>(U, n, x, Y0 + Geo::col_off(ty, Geo::CW * gj), v, vec);
-    }
-  }
-  if (bi != bj) {
-#pragma unroll
-    for (int j = 0; j < TY; ++j) {
-      const int64_t y = Y0 + Geo::col_off(ty, j);
-#pragma unroll
-      for (int gi = 0; gi < Geo::GX; ++gi) {
-        int32_t v[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) v[k] = nn - count_of(acc[4 * gi + k][j]);
-        storew<4>(U, n, y, X0 + Geo::row_off(tx, 4 * gi), v, vec);
-      }
-    }
-  }
+// TMA-staged pass-1 tile (64 x 64, see tma_ring.cuh): the X and Y panels of
+// each stage come from the tensor map `tmD` of the n x n matrix (which may
+// be a row-padded copy); thresholds are read from D (row pitch n), U is
+// written with row pitch n, and R = 1/u too when R is given (focus_finish).
+// Returns false when a wait ran out of time.
+template <class Geo>
+__device__ __forceinline__ bool focus_tile_tma(const CUtensorMap* tmD, const float* __restrict__ D, int64_t n,
+                                               int32_t* __restrict__ U, int bi, int bj, float scale, bool vec,
+                                               TmaRing<2, Geo::BK>& ring, float* __restrict__ R = nullptr,
+                                               int64_t rpitch = 0) {
+  static_assert(Geo::BX == 64 && Geo::BY == 64 && Geo::TPX == 16 && Geo::TPY == 16 && Geo::GX == 1 &&
+                    Geo::GY == 1 && Geo::CW == 4,
+                "TMA tiles are 64 x 64 with 4 x 4 pairs per thread");
+  constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY;
+  int tx, ty;
+  const bool active = tile_block_64(bi, bj, n, threadIdx.x, &tx, &ty);
+  const int nstages = static_cast<int>((n + BK - 1) / BK);
+  if (threadIdx.x == 0) ring.init();
+  __syncthreads();
+  float cst[TX][TY];
+  uint64_t acc[TX][TY];
+  focus_init<Geo>(D, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, ty, scale, cst, acc);
+  const CUtensorMap* const maps[2] = {tmD, tmD};
+  const int cols[2] = {bi * 64, bj * 64};
+  const bool ok = tma_pipeline(ring, nstages, [&](int q) { ring.issue(q, maps, cols); },
+                               [&](int, int buf) {
+                                 if (active)
+                                   focus_stage<Geo>(ring.panel(buf, 0), ring.panel(buf, 1), tx, ty, scale, cst, acc);
+                               });
+  __syncthreads();
+  if (threadIdx.x == 0) ring.inval();
+  // off the diagonal, or for an above-diagonal block of a diagonal tile,
+  // the block's mirror is written too
+  if (ok && active)
+    focus_finish<Geo>(U, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, ty, tx != ty || bi != bj, vec, acc, R, rpitch);
+  return ok;
 }
 
 }  // namespace pald

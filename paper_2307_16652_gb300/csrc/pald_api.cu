@@ -168,10 +168,13 @@ pald_status pald_tie_map(const float* D, int64_t n, uint32_t* map, pald_stream_t
 }
 
 pald_status pald_check_faults(pald_stream_t stream) {
-  uint32_t faults = 0;
-  cudaError_t e = take_cohesion_faults(&faults, reinterpret_cast<cudaStream_t>(stream));
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t f1 = 0, f2 = 0, f3 = 0;
+  cudaError_t e = take_focus_faults(&f1, s);
+  if (e == cudaSuccess) e = take_cohesion_faults(&f2, s);
+  if (e == cudaSuccess) e = take_batched_faults(&f3, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  return faults ? PALD_ERR_TIMEOUT : PALD_OK;
+  return (f1 | f2 | f3) ? PALD_ERR_TIMEOUT : PALD_OK;
 }
 
 int32_t pald_schedule_count(void) { return kScheduleCount; }

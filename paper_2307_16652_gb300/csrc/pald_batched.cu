@@ -2,17 +2,20 @@
 // launch per pass.
 //
 // Host side: the orders and offsets are checked, every matrix is cut into
-// upper-triangle tile pairs, and the tiles of all matrices are put in one
-// work list ordered by cost (largest matrices first: a tile's cost is
+// upper-triangle 64 x 64 tile pairs, and the tiles of all matrices are put in
+// one work list ordered by cost (largest matrices first: a tile's cost is
 // proportional to its matrix order, and longest-first keeps the tail short).
-// The list, the per-matrix descriptors, scan results and tie maps live in one
-// device allocation owned by a cached plan; the scan, tie-map, pass-1 and
-// pass-2 launches (plus the resets) are captured once into a CUDA graph and
-// replayed on later calls with the same arguments.
+// Every matrix gets a row-padded copy of D (row pitch rounded up to a
+// multiple of 4 floats, the 16-byte pitch TMA needs) and a row-padded R, and
+// one TMA tensor map for each.  The list, the descriptors, scan results, tie
+// maps, tensor maps and padded buffers live in one device allocation owned by
+// a cached plan; the launches (plus the resets) are captured once into a CUDA
+// graph and replayed on later calls with the same arguments.
 //
 // Device side: each persistent CTA takes the next work item from a global
-// atomic counter and runs the same tile code as the single-matrix kernels.
-// There is no spin-wait anywhere: a CTA that finds the list exhausted exits.
+// atomic counter and runs the TMA tile code of the single-matrix kernels on
+// the item's matrix.  A CTA that finds the list exhausted exits; the only
+// waits are the bounded mbarrier waits of the TMA ring.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -31,33 +34,59 @@ pald_opts opts_or_default(const pald_opts* o);
 
 namespace {
 
-using FG = FocusS0;     // 64 x 64 super-tiles, one CTA each
-using CG = CohesionS0;  // 64 x 64 super-tiles, one CTA each
-constexpr int kBF = FG::B;
-constexpr int kBC = CG::B;
-constexpr int kScanBlocksPerMatrix = 4;
-constexpr int kTieBlocksPerMatrix = 8;
-constexpr int kRecipBlocksPerMatrix = 8;
+using FG = FocusS7;     // 64 x 64 tiles, 32-deep TMA stages
+using CG = CohesionS7;  // 64 x 64 tiles, 32-deep TMA stages
+static_assert(FG::B == 64 && CG::B == 64 && FG::H == 1 && CG::H == 1, "both passes share one tile list");
+constexpr int kB = 64;
+constexpr int kTieBlocksPerMatrix = 16;
 constexpr int kMaxGridY = 65535;  // matrices beyond it are strided over blockIdx.y
+constexpr int kMaxBatchedN = 4096;
+constexpr int kTieWordsBatched = ((kMaxBatchedN + kTieGroup - 1) / kTieGroup + 31) / 32;
 
-// Smallest positive and largest entry of every matrix: matrices along
-// blockIdx.y, each matrix's entries strided over blockIdx.x.
-__global__ void __launch_bounds__(256) batched_scan_kernel(const float* __restrict__ D,
-                                                           const MatrixDesc* __restrict__ mats,
-                                                           ScanResult* __restrict__ scans, int count) {
+// Set by a CTA whose bounded wait gave up (never in normal operation).
+__device__ uint32_t g_batched_faults;
+
+// Descriptor of matrix m beyond MatrixDesc: where its padded copies and its
+// tensor maps are.
+struct PadDesc {
+  int64_t off_p;  // element offset of the padded D and R copies
+  int64_t pitch;  // their row pitch (n rounded up to a multiple of 4)
+};
+
+// One pass over every row of every matrix (matrices along blockIdx.y, rows
+// strided over blockIdx.x, one CTA per row at a time): the row's repeats go
+// into the matrix's tie map (zeroed before), the row is copied into the
+// padded layout, and the smallest positive and largest entries into the
+// matrix's scan summary (zeroed before).
+struct PrepVisit {
+  float* dst;  // padded row
+  uint32_t* inv_min;
+  uint32_t* mx;
+  __device__ __forceinline__ void operator()(int64_t c, float d) const {
+    dst[c] = d;
+    const uint32_t b = __float_as_uint(d);
+    if (b < 0x7f800000u) {
+      if (b != 0u) *inv_min = max(*inv_min, ~b);
+      *mx = max(*mx, b);
+    }
+  }
+};
+
+__global__ void __launch_bounds__(TieSmall::kThreads) batched_prep_kernel(const float* __restrict__ D,
+                                                                          const MatrixDesc* __restrict__ mats,
+                                                                          const PadDesc* __restrict__ pads,
+                                                                          float* __restrict__ Dp,
+                                                                          ScanResult* __restrict__ scans,
+                                                                          uint32_t* __restrict__ tmaps, int count) {
+  __shared__ TieSmall::Smem sm;
   for (int m = blockIdx.y; m < count; m += gridDim.y) {
     const MatrixDesc md = mats[m];
-    const float* M = D + md.off;
-    const int64_t elems = static_cast<int64_t>(md.n) * md.n;
+    const PadDesc pd = pads[m];
+    const TieMapDims dm = tie_map_dims(md.n);
     uint32_t inv_min = 0u, mx = 0u;
-    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < elems;
-         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-      const uint32_t b = __float_as_uint(__ldg(M + i));
-      if (b < 0x7f800000u) {
-        if (b != 0u) inv_min = max(inv_min, ~b);
-        mx = max(mx, b);
-      }
-    }
+    for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x)
+      tie_map_row<TieSmall>(D + md.off, md.n, row, tmaps + md.tmap_off, dm, sm,
+                            PrepVisit{Dp + pd.off_p + row * pd.pitch, &inv_min, &mx});
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       inv_min = max(inv_min, __shfl_xor_sync(0xffffffffu, inv_min, o));
@@ -77,67 +106,58 @@ __device__ __forceinline__ int64_t next_item(int* counter, int* slot) {
   return *slot;
 }
 
+// maps[2m] is matrix m's padded D, maps[2m + 1] its padded R.
 __global__ void __launch_bounds__(FG::NT, 2) batched_focus_kernel(const float* __restrict__ D, int32_t* __restrict__ U,
+                                                               float* __restrict__ Rp,
                                                                const MatrixDesc* __restrict__ mats,
+                                                               const PadDesc* __restrict__ pads,
                                                                const ScanResult* __restrict__ scans,
+                                                               const CUtensorMap* __restrict__ maps,
                                                                const WorkItem* __restrict__ items, int64_t n_items,
                                                                int* counter) {
-  extern __shared__ __align__(16) float smem[];
+  extern __shared__ __align__(128) float smem[];
   __shared__ int slot;
+  TmaRing<2, FG::BK> ring;
+  ring.carve(smem);
   for (;;) {
     const int64_t it = next_item(counter, &slot);
     if (it >= n_items) break;
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
+    const PadDesc pd = pads[w.matrix];
     const float scale = focus_scale(scans[w.matrix].inv_min_pos_bits);
-    focus_tile<FG>(D + md.off, md.n, U + md.off, w.bi, w.bj, w.slice, scale, smem);
-  }
-}
-
-// R = 1/u for every matrix (zero diagonal): matrices along blockIdx.y.
-__global__ void __launch_bounds__(256) batched_reciprocal_kernel(const int32_t* __restrict__ U, float* __restrict__ R,
-                                                                 const MatrixDesc* __restrict__ mats, int count) {
-  for (int m = blockIdx.y; m < count; m += gridDim.y) {
-    const MatrixDesc md = mats[m];
-    const bool vec = (md.n % 4) == 0;  // offsets are multiples of 4 elements
-    for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x)
-      reciprocal_rows(U + md.off, R + md.off, md.n, row, vec);
-  }
-}
-
-// Tie maps of every matrix (zeroed before): matrices along blockIdx.y, rows
-// strided over blockIdx.x, one CTA per row at a time.
-__global__ void __launch_bounds__(TieSmall::kThreads) batched_tie_kernel(const float* __restrict__ D,
-                                                                         const MatrixDesc* __restrict__ mats,
-                                                                         uint32_t* __restrict__ tmaps, int count) {
-  __shared__ TieSmall::Smem sm;
-  for (int m = blockIdx.y; m < count; m += gridDim.y) {
-    const MatrixDesc md = mats[m];
-    const TieMapDims dm = tie_map_dims(md.n);
-    for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x)
-      tie_map_row<TieSmall>(D + md.off, md.n, row, tmaps + md.tmap_off, dm, sm);
+    if (!focus_tile_tma<FG>(maps + 2 * w.matrix, D + md.off, md.n, U + md.off, w.bi, w.bj, scale, md.n % 4 == 0,
+                            ring, Rp + pd.off_p, pd.pitch)) {
+      if (threadIdx.x == 0) atomicOr(&g_batched_faults, 1u);
+      break;
+    }
   }
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(CG::NT, 2) batched_cohesion_kernel(const float* __restrict__ D,
-                                                                     const float* __restrict__ R,
                                                                      float* __restrict__ C,
                                                                      const MatrixDesc* __restrict__ mats,
                                                                      const ScanResult* __restrict__ scans,
                                                                      const uint32_t* __restrict__ tmaps,
-                                                                  const WorkItem* __restrict__ items,
-                                                                  int64_t n_items, int* counter) {
-  extern __shared__ __align__(16) float smem[];
+                                                                     const CUtensorMap* __restrict__ maps,
+                                                                     const WorkItem* __restrict__ items,
+                                                                     int64_t n_items, int* counter) {
+  extern __shared__ __align__(128) float smem[];
   __shared__ int slot;
+  TmaRing<4, CG::BK> ring;
+  uint32_t* tie_words = reinterpret_cast<uint32_t*>(ring.carve(smem));
   for (;;) {
     const int64_t it = next_item(counter, &slot);
     if (it >= n_items) break;
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
     const float S = focus_scale(scans[w.matrix].inv_min_pos_bits);
-    cohesion_tile<CG, MODE>(D + md.off, R + md.off, md.n, C + md.off, tmaps + md.tmap_off, S, w.bi, w.bj, w.slice,
-                            smem);
+    if (!cohesion_tile_tma<CG, MODE>(maps + 2 * w.matrix, maps + 2 * w.matrix + 1, D + md.off, md.n, C + md.off,
+                                     tmaps + md.tmap_off, S, w.bi, w.bj, md.n % 4 == 0, ring, tie_words)) {
+      if (threadIdx.x == 0) atomicOr(&g_batched_faults, 1u);
+      break;
+    }
   }
 }
 
@@ -192,39 +212,39 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, const float* D, int32_t* U, float* C,
                        const pald_opts& o, int device, Plan* out) {
-  // descriptors and tile lists
+  // descriptors, padded layout and the tile list (shared by both passes)
   std::vector<MatrixDesc> mats(count);
+  std::vector<PadDesc> pads(count);
   std::vector<int> order(count);
-  int64_t tmap_words = 0;
+  int64_t tmap_words = 0, pad_elems = 0;
   for (int i = 0; i < count; ++i) {
-    const int64_t Tf = (ns[i] + kBF - 1) / kBF, Tc = (ns[i] + kBC - 1) / kBC;
-    mats[i] = MatrixDesc{offs[i], static_cast<int32_t>(ns[i]), static_cast<int32_t>(Tf * (Tf + 1) / 2),
-                         static_cast<int32_t>(Tc * (Tc + 1) / 2), 0, tmap_words};
+    const int64_t T = (ns[i] + kB - 1) / kB;
+    const int32_t tiles = static_cast<int32_t>(T * (T + 1) / 2);
+    mats[i] = MatrixDesc{offs[i], static_cast<int32_t>(ns[i]), tiles, tiles, 0, tmap_words};
     tmap_words += tie_map_words(ns[i]);
+    const int64_t pitch = (ns[i] + 3) / 4 * 4;
+    pads[i] = PadDesc{pad_elems, pitch};
+    pad_elems += ns[i] * pitch;
     order[i] = i;
   }
   // longest-processing-time first: a tile costs ~ n (its streamed dimension)
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
-  std::vector<WorkItem> fitems, citems;
+  std::vector<WorkItem> items;
   for (int i : order) {
-    const int Tf = static_cast<int>((ns[i] + kBF - 1) / kBF), Tc = static_cast<int>((ns[i] + kBC - 1) / kBC);
-    for (int bi = 0; bi < Tf; ++bi)
-      for (int bj = bi; bj < Tf; ++bj)
-        for (int h = 0; h < FG::H; ++h) fitems.push_back(WorkItem{i, bi, bj, h});
-    for (int bi = 0; bi < Tc; ++bi)
-      for (int bj = bi; bj < Tc; ++bj)
-        for (int h = 0; h < CG::H; ++h) citems.push_back(WorkItem{i, bi, bj, h});
+    const int T = static_cast<int>((ns[i] + kB - 1) / kB);
+    for (int bi = 0; bi < T; ++bi)
+      for (int bj = bi; bj < T; ++bj) items.push_back(WorkItem{i, bi, bj, 0});
   }
   const size_t o_mats = 0;
-  const size_t o_scans = align_up(o_mats + sizeof(MatrixDesc) * count, 256);
-  const size_t o_fitems = align_up(o_scans + sizeof(ScanResult) * count, 256);
-  const size_t o_citems = align_up(o_fitems + sizeof(WorkItem) * fitems.size(), 256);
-  const size_t o_counters = align_up(o_citems + sizeof(WorkItem) * citems.size(), 256);
-  int64_t r_elems = 0;  // R uses the same offsets as D, U and C
-  for (int i = 0; i < count; ++i) r_elems = std::max<int64_t>(r_elems, offs[i] + ns[i] * ns[i]);
+  const size_t o_pads = align_up(o_mats + sizeof(MatrixDesc) * count, 256);
+  const size_t o_scans = align_up(o_pads + sizeof(PadDesc) * count, 256);
+  const size_t o_items = align_up(o_scans + sizeof(ScanResult) * count, 256);
+  const size_t o_counters = align_up(o_items + sizeof(WorkItem) * items.size(), 256);
   const size_t o_tmaps = align_up(o_counters + 256, 256);
-  const size_t o_recip = align_up(o_tmaps + sizeof(uint32_t) * static_cast<size_t>(tmap_words), 256);
-  const size_t total = o_recip + sizeof(float) * static_cast<size_t>(r_elems);
+  const size_t o_maps = align_up(o_tmaps + sizeof(uint32_t) * static_cast<size_t>(tmap_words), 256);
+  const size_t o_dpad = align_up(o_maps + sizeof(CUtensorMap) * 2 * static_cast<size_t>(count), 256);
+  const size_t o_rpad = align_up(o_dpad + sizeof(float) * static_cast<size_t>(pad_elems), 256);
+  const size_t total = o_rpad + sizeof(float) * static_cast<size_t>(pad_elems);
 
   Plan p;
   p.device = device;
@@ -232,15 +252,24 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   if (e != cudaSuccess) return cuda_fail(e);
   char* base = static_cast<char*>(p.dev_mem);
   auto* d_mats = reinterpret_cast<MatrixDesc*>(base + o_mats);
+  auto* d_pads = reinterpret_cast<PadDesc*>(base + o_pads);
   auto* d_scans = reinterpret_cast<ScanResult*>(base + o_scans);
-  auto* d_fitems = reinterpret_cast<WorkItem*>(base + o_fitems);
-  auto* d_citems = reinterpret_cast<WorkItem*>(base + o_citems);
+  auto* d_items = reinterpret_cast<WorkItem*>(base + o_items);
   auto* d_counters = reinterpret_cast<int*>(base + o_counters);
   auto* d_tmaps = reinterpret_cast<uint32_t*>(base + o_tmaps);
-  auto* d_recip = reinterpret_cast<float*>(base + o_recip);
-  e = cudaMemcpy(d_mats, mats.data(), sizeof(MatrixDesc) * count, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_fitems, fitems.data(), sizeof(WorkItem) * fitems.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_citems, citems.data(), sizeof(WorkItem) * citems.size(), cudaMemcpyHostToDevice);
+  auto* d_maps = reinterpret_cast<CUtensorMap*>(base + o_maps);
+  auto* d_dpad = reinterpret_cast<float*>(base + o_dpad);
+  auto* d_rpad = reinterpret_cast<float*>(base + o_rpad);
+  // tensor maps of the padded copies (their addresses are fixed by the plan)
+  std::vector<CUtensorMap> maps(2 * static_cast<size_t>(count));
+  for (int i = 0; i < count && e == cudaSuccess; ++i) {
+    e = encode_panel_map(&maps[2 * i], d_dpad + pads[i].off_p, ns[i], pads[i].pitch, FG::BK);
+    if (e == cudaSuccess) e = encode_panel_map(&maps[2 * i + 1], d_rpad + pads[i].off_p, ns[i], pads[i].pitch, CG::BK);
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(d_mats, mats.data(), sizeof(MatrixDesc) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_pads, pads.data(), sizeof(PadDesc) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     destroy_plan(p);
     return cuda_fail(e);
@@ -255,8 +284,8 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     g_capture_stream[device] = cs;
   }
   const bool plain = o.accum_mode == PALD_ACCUM_PLAIN;
-  const int fsmem = FocusSmem<FG>::FLOATS * static_cast<int>(sizeof(float));
-  const int csmem = CohesionSmem<CG>::FLOATS * static_cast<int>(sizeof(float));
+  const int fsmem = TmaRing<2, FG::BK>::BYTES + 128;
+  const int csmem = TmaRing<4, CG::BK>::BYTES + 128 + 4 * kTieWordsBatched;
   const int gf = resident_ctas(reinterpret_cast<const void*>(batched_focus_kernel), FG::NT, fsmem);
   const void* cfn = plain ? reinterpret_cast<const void*>(batched_cohesion_kernel<PALD_ACCUM_PLAIN>)
                           : reinterpret_cast<const void*>(batched_cohesion_kernel<PALD_ACCUM_COMPENSATED>);
@@ -265,6 +294,7 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     destroy_plan(p);
     return cuda_fail(cudaErrorInvalidValue);
   }
+  const int64_t n_items = static_cast<int64_t>(items.size());
 
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
@@ -272,17 +302,16 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     cudaMemsetAsync(d_scans, 0, sizeof(ScanResult) * count, cs);
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), cs);
     cudaMemsetAsync(d_tmaps, 0, sizeof(uint32_t) * static_cast<size_t>(tmap_words), cs);
-    batched_scan_kernel<<<dim3(kScanBlocksPerMatrix, gy), 256, 0, cs>>>(D, d_mats, d_scans, count);
-    batched_tie_kernel<<<dim3(kTieBlocksPerMatrix, gy), TieSmall::kThreads, 0, cs>>>(D, d_mats, d_tmaps, count);
-    batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_mats, d_scans, d_fitems,
-                                                static_cast<int64_t>(fitems.size()), d_counters);
-    batched_reciprocal_kernel<<<dim3(kRecipBlocksPerMatrix, gy), 256, 0, cs>>>(U, d_recip, d_mats, count);
+    batched_prep_kernel<<<dim3(kTieBlocksPerMatrix, gy), TieSmall::kThreads, 0, cs>>>(D, d_mats, d_pads, d_dpad,
+                                                                                      d_scans, d_tmaps, count);
+    batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_rpad, d_mats, d_pads, d_scans, d_maps, d_items, n_items,
+                                                    d_counters);
     if (plain)
-      batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, csmem, cs>>>(
-          D, d_recip, C, d_mats, d_scans, d_tmaps, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
+      batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, csmem, cs>>>(D, C, d_mats, d_scans, d_tmaps, d_maps,
+                                                                          d_items, n_items, d_counters + 1);
     else
       batched_cohesion_kernel<PALD_ACCUM_COMPENSATED><<<gc, CG::NT, csmem, cs>>>(
-          D, d_recip, C, d_mats, d_scans, d_tmaps, d_citems, static_cast<int64_t>(citems.size()), d_counters + 1);
+          D, C, d_mats, d_scans, d_tmaps, d_maps, d_items, n_items, d_counters + 1);
     cudaError_t launch_err = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &p.graph);
     if (e == cudaSuccess && launch_err != cudaSuccess) e = launch_err;
@@ -297,6 +326,16 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
 }
 
 }  // namespace
+
+cudaError_t take_batched_faults(uint32_t* out, cudaStream_t s) {
+  uint32_t zero = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(out, g_batched_faults, sizeof(uint32_t), 0, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && *out != 0u)
+    e = cudaMemcpyToSymbolAsync(g_batched_faults, &zero, sizeof(uint32_t), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e;
+}
 
 }  // namespace pald
 
@@ -315,7 +354,7 @@ pald_status pald_batched(int32_t count, const int64_t* n_host, const int64_t* of
   std::vector<std::pair<int64_t, int64_t>> spans(count);
   for (int i = 0; i < count; ++i) {
     const int64_t n = n_host[i], off = off_host[i];
-    if (n < 2 || n > 4096 || off < 0 || (off % 4) != 0) return PALD_ERR_INVALID_ARG;
+    if (n < 2 || n > kMaxBatchedN || off < 0 || (off % 4) != 0) return PALD_ERR_INVALID_ARG;
     spans[i] = {off, off + n * n};
   }
   std::sort(spans.begin(), spans.end());

@@ -15,7 +15,7 @@ __global__ void __launch_bounds__(256) reciprocal_kernel(const int32_t* __restri
                                                          int64_t n) {
   const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(U) % 16) == 0 &&
                    (reinterpret_cast<uintptr_t>(R) % 16) == 0;
-  for (int64_t row = blockIdx.x; row < n; row += gridDim.x) reciprocal_rows(U, R, n, row, vec);
+  for (int64_t row = blockIdx.x; row < n; row += gridDim.x) reciprocal_rows(U, n, R, n, row, vec);
 }
 
 template <class Geo, int MODE, int MINB>
@@ -57,8 +57,11 @@ __global__ void __launch_bounds__(CohesionS7::NT, 2)
   extern __shared__ __align__(128) float smem_tma[];
   int bi, bj, slice;
   decode_tile(blockIdx.x, T, 1, &bi, &bj, &slice);
+  TmaRing<4, CohesionS7::BK> ring;
+  uint32_t* tie_words = reinterpret_cast<uint32_t*>(ring.carve(smem_tma));
   const float S = focus_scale(scan->inv_min_pos_bits);
-  if (!cohesion_tile_tma<CohesionS7, MODE>(&tmD, &tmR, n, C, D, tmap, S, bi, bj, smem_tma) && threadIdx.x == 0)
+  if (!cohesion_tile_tma<CohesionS7, MODE>(&tmD, &tmR, D, n, C, tmap, S, bi, bj, true, ring, tie_words) &&
+      threadIdx.x == 0)
     atomicOr(&g_cohesion_faults, 1u);
 }
 
@@ -76,10 +79,10 @@ cudaError_t launch_tma(const float* D, const float* R, int64_t n, float* C, cons
   const int64_t ctas = T * (T + 1) / 2;
   if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
   CUtensorMap mD, mR;
-  cudaError_t e = encode_panel_map(&mD, D, n, Geo::BK);
-  if (e == cudaSuccess) e = encode_panel_map(&mR, R, n, Geo::BK);
+  cudaError_t e = encode_panel_map(&mD, D, n, n, Geo::BK);
+  if (e == cudaSuccess) e = encode_panel_map(&mR, R, n, n, Geo::BK);
   if (e != cudaSuccess) return e;
-  const int smem = CohesionTmaSmem<Geo>::bytes(n);
+  const int smem = CohesionTmaSmem<Geo>::bytes(n);  // TMA ring + tie words
   static bool attr_set = false;  // idempotent: racing setters write the same value
   if (!attr_set) {
     e = cudaFuncSetAttribute(cohesion_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -128,7 +131,7 @@ cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s) {
   return e;
 }
 
-cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int rows) {
+cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int64_t pitch, int rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -139,7 +142,7 @@ cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};  // {columns, rows}
-  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(n) * sizeof(float)};           // row pitch, bytes
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch) * sizeof(float)};       // row pitch, bytes
   const cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(rows)};
   const cuuint32_t elem[2] = {1u, 1u};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,

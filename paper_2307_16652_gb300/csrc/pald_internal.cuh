@@ -198,11 +198,14 @@ cudaError_t launch_tie_map(const float* D, int64_t n, uint32_t* map, cudaStream_
 // `scan` is the matrix's scan summary (launch_scan), for the pass-1 scale.
 cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
                             const ScanResult* scan, int accum_mode, int schedule, cudaStream_t s);
-// Reads and clears the device fault word of the pass-2 kernels (nonzero: a
-// bounded wait gave up).  Synchronises `s`.
+// Read and clear the device fault words of the pass-1, pass-2 and batched
+// kernels (nonzero: a bounded wait gave up).  Synchronise `s`.
 cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s);
-// Tensor map of an n x n FP32 row-major matrix with boxes of `rows` x 64.
-cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int rows);
+cudaError_t take_focus_faults(uint32_t* out, cudaStream_t s);
+cudaError_t take_batched_faults(uint32_t* out, cudaStream_t s);
+// Tensor map of an n x n FP32 row-major matrix stored with row pitch `pitch`
+// elements (a multiple of 4), with boxes of `rows` x 64.
+cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int64_t pitch, int rows);
 
 // Batched: descriptors of every matrix, and a flat list of tile work items.
 struct MatrixDesc {

@@ -19,7 +19,7 @@ using FocusS3 = TileGeom<128, 2, 2, 1, 4, 16>;   // 8x4 pairs/thread, 128x64 CTA
 using FocusS4 = TileGeom<64, 2, 1, 1, 4, 32>;    // 64x32 CTA tiles, 128 threads
 using FocusS5 = TileGeom<64, 1, 1, 1, 4, 64, 16>;  // 64-deep stages, partly unrolled
 using FocusS6 = TileGeom<128, 2, 2, 1, 4, 32>;   // 8x4 pairs/thread, 32-deep
-using FocusS7 = FocusS2;                         // (schedule 7 is a pass-2 variant)
+using FocusS7 = FocusS2;                         // S2's tile, TMA-staged
 
 using CohesionS0 = TileGeom<64, 1, 1, 1, 4, 16>;  // 4x4 pairs/thread, 256 threads
 using CohesionS1 = TileGeom<32, 1, 1, 1, 4, 16>;  // small matrices, 64 threads
@@ -42,6 +42,8 @@ inline int sm_count() {
 //   cohesion n=1024: s4 0.259 | 2048: s4 1.41 | 4096: s3 10.29 | 8192: s3 78.8 | 16384: s3 618.8
 // Orders below 1024 take the 32-wide tiles so that the launch still covers
 // the GPU.
+// (Schedule 7, TMA-staged, is no faster for pass 1 on one large matrix:
+// its per-thread copies were not the bound.)
 inline int default_focus_schedule(int64_t n) { return n < 1024 ? 1 : 2; }
 
 // Schedule 7 (TMA) needs n % 4 == 0 and aligned buffers; otherwise it runs

@@ -77,17 +77,23 @@ __device__ __forceinline__ void tie_mark(uint32_t* map, const TieMapDims& dm, in
   atomicOr(map + (a * dm.nb + b) * dm.wpp + (g >> 5), 1u << (g & 31));
 }
 
+struct NoVisit {
+  __device__ __forceinline__ void operator()(int64_t, float) const {}
+};
+
 // All Cfg::kThreads threads of the CTA process row `row` of the n x n matrix
-// at `Dm` into `map` (already zeroed).  Contains barriers: call uniformly.
-template <class Cfg>
+// at `Dm` into `map` (already zeroed).  `visit(c, d_row,c)` sees every entry
+// of the row once (during the first hash pass).  Contains barriers: call
+// uniformly.
+template <class Cfg, class Visit = NoVisit>
 __device__ __forceinline__ void tie_map_row(const float* __restrict__ Dm, int64_t n, int64_t row, uint32_t* map,
-                                            const TieMapDims& dm, typename Cfg::Smem& sm) {
+                                            const TieMapDims& dm, typename Cfg::Smem& sm, Visit visit = Visit()) {
   constexpr int NT = Cfg::kThreads, SLOTS = Cfg::kSlots, CAP = Cfg::kDupCap;
   const float* drow = Dm + row * n;
   const int64_t brow = row / kTieBlock;
   const int parts = static_cast<int>((n + Cfg::kPart - 1) / Cfg::kPart);
   bool dirty = false;
-  for (int part = 0; part < parts && !dirty; ++part) {
+  for (int part = 0; part < parts && !dirty; ++part) {  // part 0 always runs
     for (int i = threadIdx.x; i < SLOTS; i += NT) sm.key[i] = kTieEmpty;
     if (threadIdx.x == 0) {
       sm.ndup = 0;
@@ -95,8 +101,10 @@ __device__ __forceinline__ void tie_map_row(const float* __restrict__ Dm, int64_
     }
     __syncthreads();
     for (int64_t c = threadIdx.x; c < n; c += NT) {
+      const float d = __ldg(drow + c);
+      if (part == 0) visit(c, d);
       // +0.0f turns a stray -0.0 into +0.0 (equal under comparison)
-      const uint32_t v = __float_as_uint(__fadd_rn(__ldg(drow + c), 0.0f));
+      const uint32_t v = __float_as_uint(__fadd_rn(d, 0.0f));
       const uint32_t h = tie_hash(v);
       if (parts > 1 && static_cast<int>((static_cast<uint64_t>(h) * static_cast<uint64_t>(parts)) >> 32) != part)
         continue;

@@ -81,4 +81,41 @@ __host__ __device__ __forceinline__ void decode_tile(int64_t t, int64_t T, int H
   }
 }
 
+// Thread placement in a 64 x 64 tile of 16 x 16 thread blocks (4 x 4 pairs
+// each) of an n x n matrix.  A full off-diagonal tile gives thread t block
+// (t % 16, t / 16).  Otherwise only the blocks that hold pairs of the matrix
+// are handed out, to threads 0, 1, ... in order, so that whole warps drop
+// out: on a ragged edge tile the blocks inside the matrix, and on a diagonal
+// tile (X == Z) only the blocks (a, b) with a <= b, since a block below the
+// diagonal repeats, with rows and columns swapped, what its mirror above
+// computes.  Threads without a block only take part in the barriers.
+// Returns whether thread t owns a block.
+__device__ __forceinline__ bool tile_block_64(int bi, int bj, int64_t n, int t, int* a, int* b) {
+  const int64_t rx = n - int64_t(bi) * 64, rz = n - int64_t(bj) * 64;
+  const int ax = rx >= 64 ? 16 : static_cast<int>((rx + 3) / 4);  // blocks holding rows of the matrix
+  const int az = rz >= 64 ? 16 : static_cast<int>((rz + 3) / 4);
+  *a = 0;
+  *b = 0;  // placement of a thread without a block (its setup work is harmless)
+  if (bi != bj) {
+    if (ax == 16 && az == 16) {
+      *a = t % 16;
+      *b = t / 16;
+      return true;
+    }
+    if (t >= ax * az) return false;
+    *a = t % ax;
+    *b = t / ax;
+    return true;
+  }
+  int r = 0;  // upper triangle of the ax x ax blocks, row by row
+  while (r < ax && t >= ax - r) {
+    t -= ax - r;
+    ++r;
+  }
+  if (r == ax) return false;
+  *a = r;
+  *b = r + t;
+  return true;
+}
+
 }  // namespace pald
