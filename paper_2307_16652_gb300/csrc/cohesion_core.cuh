@@ -49,9 +49,11 @@
 // 4 * 1/2 plus the carried error, so |H| >= |S| always holds and Fast2Sum
 // (three adds, done as packed f32x2 ops on both accumulators at once) is
 // error-free.  Its exact error becomes the start of the next partial, so
-// nothing is lost between chunks.  At the end H - B + S is formed in FP64,
-// multiplied by 1/(n-1) in FP64 and rounded once to FP32.
-// PALD_ACCUM_PLAIN keeps one FP32 running sum (the precision baseline).
+// nothing is lost between chunks.  At the end H - B + S is formed exactly as
+// a two-float value, multiplied by 1/(n-1) (also two floats) and rounded once
+// to FP32: the precision of an FP64 merge, without the FP64 pipe (two_sum,
+// mul_pair below).  PALD_ACCUM_PLAIN keeps one FP32 running sum (the
+// precision baseline), normalised the same way.
 #pragma once
 
 #include "focus_core.cuh"
@@ -106,6 +108,38 @@ __device__ __forceinline__ void cohesion_step_short(uint64_t& sacc, float a1, fl
 // lane of pair (z, x), and a symmetric phase gives both the same chunking,
 // so every schedule, both forms and the batched path stay bit-identical.
 __host__ __device__ constexpr int fold_phase(int i, int j) { return ((i + j) & 1) ? 1 : 3; }
+
+// ---------------------------------------------------------------------------
+// Final merge in two-float arithmetic.  GB300 runs FP64 at about two
+// operations per clock per SM, so a per-entry FP64 merge costs more than the
+// inner loop of a short tile; these error-free transformations give the same
+// result (the exact merge rounded once to FP32, up to 2^-46 relative).
+
+// TwoSum (Knuth): s + e == a + b exactly, s = RN(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
+}
+
+// 1/m as hi + lo for a positive integer m < 2^24: hi = RN(1/m), and
+// lo = (1 - hi*m) * hi, where 1 - hi*m comes out of one FMA exactly (the
+// residual of a correctly rounded reciprocal), so hi + lo = 1/m to about
+// 2^-47 relative.
+__device__ __forceinline__ void inverse_pair(int64_t m, float& hi, float& lo) {
+  const float mf = static_cast<float>(m);
+  hi = __frcp_rn(mf);
+  lo = __fmul_rn(__fmaf_rn(-hi, mf, 1.0f), hi);
+}
+
+// RN((a + b) * (ih + il)) for a two-float a + b (|b| <= ulp(a)) and a
+// two-float ih + il, up to 2^-46 relative: a*ih is split exactly by an FMA,
+// the small cross terms are added to its error, and one final add rounds.
+__device__ __forceinline__ float mul_pair(float a, float b, float ih, float il) {
+  const float m = __fmul_rn(a, ih);
+  const float t = __fmaf_rn(a, ih, -m);
+  return __fadd_rn(m, __fmaf_rn(a, il, __fmaf_rn(b, ih, t)));
+}
 
 // Packed f32x2 add and subtract (one instruction for both lanes).
 __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
@@ -236,17 +270,21 @@ __device__ __forceinline__ void cohesion_finish(float* __restrict__ C, int64_t n
                                                 int tz, bool mirror, bool vec,
                                                 const uint64_t (&sacc)[Geo::TX][Geo::TY],
                                                 const uint64_t (&hacc)[Geo::TX][Geo::TY]) {
-  const double inv = 1.0 / static_cast<double>(n - 1);
-  // value of the (xz or zx) lane: compensated (H - B) + S in FP64, or plain S
+  float ih, il;
+  inverse_pair(n - 1, ih, il);
+  // value of the (xz or zx) lane: compensated (H - B) + S, or plain S, times
+  // 1/(n-1), formed exactly as a two-float value and rounded once
   auto finish = [&](uint64_t h2, uint64_t s2, bool zx) -> float {
     float hl, hh, sl, sh;
     unpack2(h2, hl, hh);
     unpack2(s2, sl, sh);
     const float h = zx ? hh : hl, s = zx ? sh : sl;
-    if (MODE == PALD_ACCUM_COMPENSATED)
-      return static_cast<float>(((static_cast<double>(h) - static_cast<double>(kMergeBias)) +
-                                 static_cast<double>(s)) * inv);
-    return static_cast<float>(static_cast<double>(s) * inv);
+    if (MODE == PALD_ACCUM_COMPENSATED) {
+      float p, e;
+      two_sum(__fsub_rn(h, kMergeBias), s, p, e);  // H - B is exact: B is a multiple of H's unit
+      return mul_pair(p, e, ih, il);
+    }
+    return mul_pair(s, 0.f, ih, il);
   };
 #pragma unroll
   for (int i = 0; i < Geo::TX; ++i) {
