@@ -116,7 +116,9 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
  *   C         device FP32, same layout as D; receives C for every matrix.
  * The first call for a given (count, n, off, D, U, C, opts) builds a work
  * plan and a CUDA graph (host work, and it synchronises `stream`); later calls
- * with the same arguments only launch the graph.  pald_release() frees them.
+ * with the same arguments only launch the graph.  A plan holds device memory
+ * of about twice the packed D (row-padded copies of D and of R = 1/u, whose
+ * 16-byte row pitch the TMA copies need) until pald_release() frees it.
  * Errors: INVALID_ARG (bad count, n_i, misaligned or overlapping offsets);
  * validation errors; CUDA; NO_MEMORY.
  */
@@ -126,9 +128,10 @@ pald_status pald_batched(int32_t count, const int64_t* n_host, const int64_t* of
 
 /*
  * pald_host - convenience call on HOST buffers: copies D to the device, runs
- * both passes, copies U and C back, and synchronises.  Device buffers are
- * allocated and freed inside the call.  Pinned host memory makes the copies
- * faster but is not required.
+ * both passes, copies U and C back, and synchronises.  U's copy back runs on
+ * a second stream while pass 2 computes.  Device buffers are allocated and
+ * freed inside the call.  Pinned host memory makes the copies faster and
+ * lets U's copy overlap pass 2, but is not required.
  *   D_host  host n x n FP32; U_host host n x n int32; C_host host n x n FP32.
  * Errors: as pald_focus and pald_cohesion.
  */

@@ -127,34 +127,55 @@ pald_status pald_validate(const float* D, int64_t n, pald_stream_t stream) {
 pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_host, const pald_opts* opts) {
   if (!D_host || !U_host || !C_host || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
   const size_t bytes = static_cast<size_t>(n) * static_cast<size_t>(n) * 4u;
-  cudaStream_t s = nullptr;
+  // s runs the passes; s2 copies U back while pass 2 runs (pass 2 only reads U)
+  cudaStream_t s = nullptr, s2 = nullptr;
+  cudaEvent_t u_ready = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return cuda_fail(e);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&u_ready, cudaEventDisableTiming);
   float* dD = nullptr;
   int32_t* dU = nullptr;
   float* dC = nullptr;
   pald_status st = PALD_OK;
-  do {
+  bool u_copy_issued = false;
+  while (e == cudaSuccess) {
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&dD), bytes, s)) != cudaSuccess) break;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&dU), bytes, s)) != cudaSuccess) break;
     if ((e = cudaMallocAsync(reinterpret_cast<void**>(&dC), bytes, s)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(dD, D_host, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     st = pald_focus(dD, n, dU, opts, reinterpret_cast<pald_stream_t>(s));
     if (st != PALD_OK) break;
+    if ((e = cudaEventRecord(u_ready, s)) != cudaSuccess) break;
+    if ((e = cudaStreamWaitEvent(s2, u_ready, 0)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(U_host, dU, bytes, cudaMemcpyDeviceToHost, s2)) != cudaSuccess) break;
+    u_copy_issued = true;
     pald_opts o2 = opts_or_default(opts);
     o2.validate = 0;  // already checked by pass 1 when asked
     st = pald_cohesion(dD, dU, n, dC, &o2, reinterpret_cast<pald_stream_t>(s));
     if (st != PALD_OK) break;
-    if ((e = cudaMemcpyAsync(U_host, dU, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
     if ((e = cudaMemcpyAsync(C_host, dC, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
-  } while (false);
+    break;
+  }
+  // U's buffer is freed only after its copy: order the frees after s2
+  cudaError_t e3 = cudaSuccess;
+  if (u_copy_issued) {
+    e3 = cudaEventRecord(u_ready, s2);
+    if (e3 == cudaSuccess) e3 = cudaStreamWaitEvent(s, u_ready, 0);
+  }
   if (dD) cudaFreeAsync(dD, s);
   if (dU) cudaFreeAsync(dU, s);
   if (dC) cudaFreeAsync(dC, s);
-  cudaError_t e2 = cudaStreamSynchronize(s);
-  cudaStreamDestroy(s);
+  cudaError_t e2 = s ? cudaStreamSynchronize(s) : cudaSuccess;
+  if (s2) {
+    cudaError_t e4 = cudaStreamSynchronize(s2);
+    if (e2 == cudaSuccess) e2 = e4;
+    cudaStreamDestroy(s2);
+  }
+  if (u_ready) cudaEventDestroy(u_ready);
+  if (s) cudaStreamDestroy(s);
   if (e != cudaSuccess) return cuda_fail(e);
   if (st != PALD_OK) return st;
+  if (e3 != cudaSuccess) return cuda_fail(e3);
   if (e2 != cudaSuccess) return cuda_fail(e2);
   return PALD_OK;
 }
