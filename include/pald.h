@@ -62,10 +62,11 @@ typedef enum pald_status {
 enum {
   /* FP32 partial sums over 4 consecutive y, folded into an FP32 running sum
    * (biased so that Fast2Sum is error-free) whose exact error is carried into
-   * the next partial; FP64 final merge, 1/(n-1) in FP64, one rounding to FP32
-   * (default). */
+   * the next partial; the final merge and the 1/(n-1) normalisation are
+   * exact two-float arithmetic with one rounding to FP32 (the precision of an
+   * FP64 merge) (default). */
   PALD_ACCUM_COMPENSATED = 0,
-  /* one FP32 running sum per entry (precision baseline), normalised in FP64 */
+  /* one FP32 running sum per entry (precision baseline), normalised the same way */
   PALD_ACCUM_PLAIN = 1
 };
 
