@@ -198,3 +198,27 @@ def test_host_entry_point_matches_device_path():
     binding.pald_host(D, Uh, Ch)
     U, C = run_gpu(D)
     assert np.array_equal(Uh, U) and np.array_equal(Ch, C)
+
+
+def test_misaligned_buffers_take_the_copy_path():
+    # TMA needs 16-byte aligned bases; views offset by one float fall back to
+    # the same tiles staged with per-thread copies, with identical bits
+    n = 256
+    D_np = inputs.small_points_matrix(np.random.default_rng(4), n, dim=3)
+    Uref, Cref = oracle.focus_and_cohesion(D_np)
+
+    def views(dtype):
+        base = torch.zeros(n * n + 4, dtype=dtype, device="cuda")
+        return base[1:1 + n * n].view(n, n)
+
+    D = views(torch.float32)
+    D.copy_(torch.from_numpy(D_np).cuda())
+    U, C = views(torch.int32), views(torch.float32)
+    assert D.data_ptr() % 16 != 0
+    binding.pald_focus(D, U)
+    binding.pald_cohesion(D, U, C)
+    Ua, Ca = run_gpu(D_np)
+    torch.cuda.synchronize()
+    assert np.array_equal(U.cpu().numpy(), Ua)
+    assert np.array_equal(C.cpu().numpy(), Ca)
+    assert_parity(U.cpu().numpy(), C.cpu().numpy(), Uref, Cref)
