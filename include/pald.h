@@ -169,6 +169,28 @@ pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, int64_t n, f
 pald_status pald_validate(const float* D, int64_t n, pald_stream_t stream);
 
 /*
+ * pald_local_depth - local depths from a cohesion matrix: L[x] = sum over z
+ * of c_xz, the local depth of x (Sec. 2: cohesion partitions local depth,
+ * eq. (LD)).  Deterministic: a fixed per-row order in two-float arithmetic,
+ * one rounding to FP32.
+ *   C  device, n x n FP32 (as written by pald_cohesion).
+ *   L  device, n FP32, written completely.
+ * Errors: INVALID_ARG (null pointer, n out of range); CUDA.
+ */
+pald_status pald_local_depth(const float* C, int64_t n, float* L, pald_stream_t stream);
+
+/*
+ * pald_strong_ties - the strong-tie mask for a threshold: T[x*n+z] = 1 when
+ * c_xz >= threshold, else 0 (Sec. 2: cohesion stronger than a random focus
+ * point would give; Sec. 7 applies a universal threshold defined outside
+ * this paper, so the caller supplies it).  The mask is directed (row x, the
+ * cohesion of z to x); a symmetric tie graph is T AND T^T or T OR T^T.
+ *   C  device, n x n FP32.  T  device, n x n uint8, written completely.
+ * Errors: INVALID_ARG (null pointer, n out of range, NaN threshold); CUDA.
+ */
+pald_status pald_strong_ties(const float* C, int64_t n, float threshold, uint8_t* T, pald_stream_t stream);
+
+/*
  * pald_tie_map - diagnostic: the tie map that pald_cohesion builds for D and
  * reads to pick, per tile and stage of 32 y, between its short inner loop
  * (valid when no one-sided tie d_xy == d_xz or d_zy == d_zx can occur) and

@@ -26,10 +26,12 @@ from .binding import (  # noqa: F401
     pald_cohesion_noalloc,
     pald_focus,
     pald_host,
+    pald_local_depth,
     pald_release,
     pald_schedule_count,
     pald_schedule_name,
     pald_status_string,
+    pald_strong_ties,
     pald_tie_map,
     pald_tie_map_words,
     pald_validate,
@@ -38,7 +40,8 @@ from .binding import (  # noqa: F401
 
 __all__ = [
     "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PaldError", "lib", "library_path", "pald_check_faults",
-    "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_release",
+    "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_local_depth",
+    "pald_release", "pald_strong_ties",
     "pald_schedule_count", "pald_schedule_name", "pald_status_string", "pald_tie_map", "pald_tie_map_words",
     "pald_validate", "pald_version",
 ]

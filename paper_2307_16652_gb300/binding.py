@@ -67,10 +67,12 @@ def _lib() -> ctypes.CDLL:
         h.pald_validate.argtypes = [vp, i64, vp]
         h.pald_tie_map.argtypes = [vp, i64, vp, vp]
         h.pald_check_faults.argtypes = [vp]
+        h.pald_local_depth.argtypes = [vp, i64, vp, vp]
+        h.pald_strong_ties.argtypes = [vp, i64, ctypes.c_float, vp, vp]
         h.pald_tie_map_words.argtypes = [i64]
         h.pald_tie_map_words.restype = i64
         for f in (h.pald_focus, h.pald_cohesion, h.pald_cohesion_noalloc, h.pald_batched, h.pald_host,
-                  h.pald_validate, h.pald_tie_map, h.pald_check_faults):
+                  h.pald_validate, h.pald_tie_map, h.pald_check_faults, h.pald_local_depth, h.pald_strong_ties):
             f.restype = ctypes.c_int
         h.pald_status_string.argtypes = [ctypes.c_int]
         h.pald_status_string.restype = ctypes.c_char_p
@@ -210,6 +212,34 @@ def pald_validate(D, *, stream=None):
 
     n = D.shape[0]
     return _lib().pald_validate(_check(D, torch.float32, n, "D"), n, _stream_ptr(stream))
+
+
+def pald_local_depth(C, L=None, *, stream=None):
+    """Local depths L[x] = sum_z C[x, z] (FP32 CUDA tensors); returns L."""
+    import torch
+
+    n = C.shape[0]
+    if L is None:
+        L = torch.empty(n, dtype=torch.float32, device=C.device)
+    if not (isinstance(L, torch.Tensor) and L.is_cuda and L.dtype == torch.float32 and L.is_contiguous()
+            and tuple(L.shape) == (n,)):
+        raise ValueError(f"L must be a contiguous float32 CUDA tensor of shape ({n},)")
+    st = _lib().pald_local_depth(_check(C, torch.float32, n, "C"), n, L.data_ptr(), _stream_ptr(stream))
+    _raise(st, "pald_local_depth")
+    return L
+
+
+def pald_strong_ties(C, threshold, T=None, *, stream=None):
+    """Mask T[x, z] = (C[x, z] >= threshold) as uint8 (CUDA tensors); returns T."""
+    import torch
+
+    n = C.shape[0]
+    if T is None:
+        T = torch.empty((n, n), dtype=torch.uint8, device=C.device)
+    st = _lib().pald_strong_ties(_check(C, torch.float32, n, "C"), n, float(threshold),
+                                 _check(T, torch.uint8, n, "T"), _stream_ptr(stream))
+    _raise(st, "pald_strong_ties")
+    return T
 
 
 def pald_tie_map_words(n: int) -> int:

@@ -62,6 +62,10 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.pald_host(None, 8, None, None, None) == INVALID
     assert lib.pald_tie_map(None, 8, fake, None) == INVALID
     assert lib.pald_tie_map(fake, 1, fake, None) == INVALID
+    assert lib.pald_local_depth(None, 8, fake, None) == INVALID
+    assert lib.pald_local_depth(fake, 1, fake, None) == INVALID
+    assert lib.pald_strong_ties(fake, 8, float("nan"), fake, None) == INVALID
+    assert lib.pald_strong_ties(fake, 8, 0.5, None, None) == INVALID
 
 
 def test_tie_map_size():
