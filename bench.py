@@ -35,7 +35,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "triplets/sec per pass, % of CUDA-core peak; batched vs plain at stated error"
 UNIT = "triplets/s"
-LAUNCHES_PER_STEP = 5          # scan, focus, tie map, reciprocal, cohesion kernels (ours)
+LAUNCHES_PER_STEP = 6          # per pass: scan + focus | scan + tie map + reciprocal + cohesion
 OPS_PER_TRIPLET = {"focus": 9, "cohesion": 18}   # lane-op budget per unique triplet
 LANES_PER_SM_CLK = 128                            # 4 SMSPs x 1 warp-instruction x 32 lanes
 
