@@ -38,12 +38,10 @@ inline int sm_count() {
 }
 
 // Defaults from the GB300 autotune table (times in ms, best per order):
-//   focus    n=1024: s2 0.127 | 2048: s4 0.52 | 4096: s2 3.52 | 8192: s2 27.1 | 16384: s2 212.7
-//   cohesion n=1024: s4 0.259 | 2048: s4 1.41 | 4096: s3 10.29 | 8192: s3 78.8 | 16384: s3 618.8
+//   focus    n=1024: s7 0.117 | 2048: s4 0.515 | 4096: s2/s7 3.52 | 8192: s2/s7 27.1
+//   cohesion n=1024: s7 0.229 | 2048: s7 1.118 | 4096: s7 7.17   | 8192: s7 54.6
 // Orders below 1024 take the 32-wide tiles so that the launch still covers
 // the GPU.
-// (Schedule 7, TMA-staged, is no faster for pass 1 on one large matrix:
-// its per-thread copies were not the bound.)
 inline int default_focus_schedule(int64_t n) { return n < 1024 ? 1 : 2; }
 
 // Schedule 7 (TMA) needs n % 4 == 0 and aligned buffers; otherwise it runs
