@@ -70,11 +70,20 @@ enum {
   PALD_ACCUM_PLAIN = 1
 };
 
+/* Bits of pald_opts.flags. */
+enum {
+  /* Pass 2 credits z to x only when d_xz < min(d_xy, d_zy): no half credit,
+   * no credit on a tie, as the paper's optimised codes do (Sec. 5).  INEXACT
+   * unless no row of D holds the same value twice; it skips the tie map and
+   * runs the short inner loop everywhere.  Pass 1 is unaffected (exact). */
+  PALD_FLAG_IGNORE_TIES = 1
+};
+
 typedef struct pald_opts {
   int32_t validate;     /* nonzero: check the input contract before computing */
   int32_t accum_mode;   /* PALD_ACCUM_COMPENSATED or PALD_ACCUM_PLAIN */
   int32_t schedule_id;  /* -1 = automatic tile schedule; >= 0 forces one (pald_schedule_name) */
-  int32_t reserved;     /* must be 0 */
+  int32_t flags;        /* 0 (exact, the default) or PALD_FLAG_IGNORE_TIES; other bits must be 0 */
 } pald_opts;          /* a NULL opts pointer means {0, PALD_ACCUM_COMPENSATED, -1, 0} */
 
 /*
@@ -147,7 +156,8 @@ pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_
  * allocating routine.  Its scratch (R = 1/u) is a fixed array built into the
  * library, 16 MiB + 256 bytes, which every GPU that loads the library holds
  * until the process exits.
- *   D, U, n, C, opts, stream  as pald_cohesion, with 2 <= n <= 2048.
+ *   D, U, n, C, opts, stream  as pald_cohesion, with 2 <= n <= 2048;
+ *   PALD_FLAG_IGNORE_TIES is not supported here (INVALID_ARG).
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture
  * begins.  Every call on a device shares the one array and overwrites it:

@@ -17,6 +17,7 @@ from __future__ import annotations
 from .binding import (  # noqa: F401
     PALD_ACCUM_COMPENSATED,
     PALD_ACCUM_PLAIN,
+    PALD_FLAG_IGNORE_TIES,
     PaldError,
     lib,
     pald_check_faults,
@@ -39,7 +40,7 @@ from .binding import (  # noqa: F401
 )
 
 __all__ = [
-    "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PaldError", "lib", "library_path", "pald_check_faults",
+    "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PALD_FLAG_IGNORE_TIES", "PaldError", "lib", "library_path", "pald_check_faults",
     "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_local_depth",
     "pald_release", "pald_strong_ties",
     "pald_schedule_count", "pald_schedule_name", "pald_status_string", "pald_tie_map", "pald_tie_map_words",

@@ -17,6 +17,7 @@ from . import build as _build
 
 PALD_ACCUM_COMPENSATED = 0
 PALD_ACCUM_PLAIN = 1
+PALD_FLAG_IGNORE_TIES = 1
 
 _STATUS = {
     0: "PALD_OK", 1: "PALD_ERR_INVALID_ARG", 2: "PALD_ERR_NOT_SYMMETRIC", 3: "PALD_ERR_BAD_DIAGONAL",
@@ -37,7 +38,7 @@ class PaldError(RuntimeError):
 
 class PaldOpts(ctypes.Structure):
     _fields_ = [("validate", ctypes.c_int32), ("accum_mode", ctypes.c_int32),
-                ("schedule_id", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("schedule_id", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -91,8 +92,9 @@ def lib() -> ctypes.CDLL:
     return _lib()
 
 
-def _opts(validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1):
-    return PaldOpts(int(bool(validate)), int(accum_mode), int(schedule_id), 0)
+def _opts(validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1, ignore_ties=False):
+    return PaldOpts(int(bool(validate)), int(accum_mode), int(schedule_id),
+                    PALD_FLAG_IGNORE_TIES if ignore_ties else 0)
 
 
 def _stream_ptr(stream):
@@ -138,12 +140,15 @@ def pald_focus(D, U, *, validate=False, schedule_id=-1, stream=None):
     return U
 
 
-def pald_cohesion(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1, stream=None):
-    """Pass 2: C[x, z] = c_xz (FP32) from D and the focus sizes U."""
+def pald_cohesion(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1, ignore_ties=False,
+                  stream=None):
+    """Pass 2: C[x, z] = c_xz (FP32) from D and the focus sizes U.
+
+    ignore_ties=True is the paper's inexact fast mode (PALD_FLAG_IGNORE_TIES)."""
     import torch
 
     n = D.shape[0]
-    o = _opts(validate, accum_mode, schedule_id)
+    o = _opts(validate, accum_mode, schedule_id, ignore_ties)
     st = _lib().pald_cohesion(_check(D, torch.float32, n, "D"), _check(U, torch.int32, n, "U"), n,
                               _check(C, torch.float32, n, "C"), ctypes.byref(o), _stream_ptr(stream))
     _raise(st, "pald_cohesion")
@@ -167,7 +172,8 @@ def pald_cohesion_noalloc(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMP
     return C
 
 
-def pald_batched(ns, offs, D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, stream=None):
+def pald_batched(ns, offs, D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, ignore_ties=False,
+                 stream=None):
     """Both passes for packed matrices: matrix i is ns[i] x ns[i] at element offs[i]."""
     import numpy as np
     import torch
@@ -181,7 +187,7 @@ def pald_batched(ns, offs, D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COM
     need = int((offs + ns * ns).max())
     if min(D.numel(), U.numel(), C.numel()) < need:
         raise ValueError("packed buffers are smaller than the last matrix")
-    o = _opts(validate, accum_mode, -1)
+    o = _opts(validate, accum_mode, -1, ignore_ties)
     st = _lib().pald_batched(len(ns), ns.ctypes.data, offs.ctypes.data, D.data_ptr(), U.data_ptr(),
                              C.data_ptr(), ctypes.byref(o), _stream_ptr(stream))
     _raise(st, "pald_batched")

@@ -19,7 +19,7 @@ pald_status cuda_fail(cudaError_t e) {
 
 bool opts_ok(const pald_opts* o) {
   if (!o) return true;
-  if (o->reserved != 0) return false;
+  if ((o->flags & ~PALD_FLAG_IGNORE_TIES) != 0) return false;
   if (o->accum_mode != PALD_ACCUM_COMPENSATED && o->accum_mode != PALD_ACCUM_PLAIN) return false;
   if (o->schedule_id < -1 || o->schedule_id >= kScheduleCount) return false;
   return true;
@@ -108,7 +108,11 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
   auto* scan = reinterpret_cast<ScanResult*>(static_cast<char*>(scratch.p) + rbytes + tbytes);
   pald_status st = scan_and_check(D, n, scan, o.validate != 0, s);
   if (st != PALD_OK) return st;
-  if ((e = launch_tie_map(D, n, tmap, s)) != cudaSuccess) return cuda_fail(e);
+  if (o.flags & PALD_FLAG_IGNORE_TIES)  // an empty map: the short (strict) form everywhere
+    e = cudaMemsetAsync(tmap, 0, static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t), s);
+  else
+    e = launch_tie_map(D, n, tmap, s);
+  if (e != cudaSuccess) return cuda_fail(e);
   if ((e = launch_reciprocal(U, R, n, s)) != cudaSuccess) return cuda_fail(e);
   if ((e = launch_cohesion(D, R, n, C, tmap, scan, o.accum_mode, o.schedule_id, s)) != cudaSuccess)
     return cuda_fail(e);

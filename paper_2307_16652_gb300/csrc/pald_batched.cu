@@ -304,6 +304,8 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     cudaMemsetAsync(d_tmaps, 0, sizeof(uint32_t) * static_cast<size_t>(tmap_words), cs);
     batched_prep_kernel<<<dim3(kTieBlocksPerMatrix, gy), TieSmall::kThreads, 0, cs>>>(D, d_mats, d_pads, d_dpad,
                                                                                       d_scans, d_tmaps, count);
+    if (o.flags & PALD_FLAG_IGNORE_TIES)  // empty maps: the short (strict) form everywhere
+      cudaMemsetAsync(d_tmaps, 0, sizeof(uint32_t) * static_cast<size_t>(tmap_words), cs);
     batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_rpad, d_mats, d_pads, d_scans, d_maps, d_items, n_items,
                                                     d_counters);
     if (plain)
@@ -383,6 +385,7 @@ pald_status pald_batched(int32_t count, const int64_t* n_host, const int64_t* of
   key.words.push_back(static_cast<int64_t>(reinterpret_cast<uintptr_t>(U)));
   key.words.push_back(static_cast<int64_t>(reinterpret_cast<uintptr_t>(C)));
   key.words.push_back(o.accum_mode);
+  key.words.push_back(o.flags);
   for (int i = 0; i < count; ++i) {
     key.words.push_back(n_host[i]);
     key.words.push_back(off_host[i]);

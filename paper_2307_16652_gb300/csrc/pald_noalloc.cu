@@ -63,6 +63,7 @@ using namespace pald;
 extern "C" pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, int64_t n, float* C,
                                              const pald_opts* opts, pald_stream_t stream) {
   if (!D || !U || !C || n < 2 || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
+  if (opts && (opts->flags & PALD_FLAG_IGNORE_TIES)) return PALD_ERR_INVALID_ARG;  // needs a tie map
   if (n > kNoAllocMaxN) return PALD_ERR_UNSUPPORTED;  // R would not fit the fixed array
   const pald_opts o = opts_or_default(opts);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -56,7 +56,7 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.pald_cohesion(fake, None, 8, fake, ctypes.byref(o), None) == INVALID
     bad = binding.PaldOpts(0, 7, -1, 0)                                           # unknown accum mode
     assert lib.pald_cohesion(fake, fake, 8, fake, ctypes.byref(bad), None) == INVALID
-    bad = binding.PaldOpts(0, 0, -1, 3)                                           # reserved != 0
+    bad = binding.PaldOpts(0, 0, -1, 2)                                           # unknown flag bit
     assert lib.pald_focus(fake, 8, fake, ctypes.byref(bad), None) == INVALID
     assert lib.pald_validate(None, 8, None) == INVALID
     assert lib.pald_host(None, 8, None, None, None) == INVALID
