@@ -171,44 +171,51 @@ __device__ __forceinline__ void unpack2(uint64_t v, float& lo, float& hi) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
 }
 
-// One pipeline stage (BK consecutive y) of a CTA tile, long or short form.
+// One pipeline stage (BK consecutive y) of a CTA tile, long or short form,
+// in chunks of Geo::UNR y: the first `kend` y of the stage (a multiple of
+// UNR; the zero-filled y past n add +0, so whole chunks of them are skipped).
 template <class Geo, int MODE, bool SHORT>
 __device__ __forceinline__ void cohesion_stage(const float* ad, const float* ar, const float* bd, const float* br,
                                                int tx, int tz, float S, const float (&cv)[Geo::TX][Geo::TY],
                                                uint64_t (&sacc)[Geo::TX][Geo::TY],
-                                               uint64_t (&hacc)[Geo::TX][Geo::TY]) {
+                                               uint64_t (&hacc)[Geo::TX][Geo::TY], int kend = Geo::BK) {
   constexpr int TX = Geo::TX, TY = Geo::TY;
-#pragma unroll Geo::UNR
-  for (int kk = 0; kk < Geo::BK; ++kk) {
-    float a1[TX], r1[TX], a2[TY], r2[TY];
+#pragma unroll 1
+  for (int k0 = 0; k0 < kend; k0 += Geo::UNR) {
 #pragma unroll
-    for (int g = 0; g < Geo::GX; ++g) {
-      lds<4>(ad + kk * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
-      lds<4>(ar + kk * Geo::BX + Geo::row_off(tx, 4 * g), r1 + 4 * g);
-    }
+    for (int k = 0; k < Geo::UNR; ++k) {
+      const int kk = k0 + k;
+      float a1[TX], r1[TX], a2[TY], r2[TY];
 #pragma unroll
-    for (int g = 0; g < Geo::GY; ++g) {
-      lds<Geo::CW>(bd + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), a2 + Geo::CW * g);
-      lds<Geo::CW>(br + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), r2 + Geo::CW * g);
-    }
-#pragma unroll
-    for (int i = 0; i < TX; ++i)
-#pragma unroll
-      for (int j = 0; j < TY; ++j) {
-        if (SHORT)
-          cohesion_step_short(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
-        else
-          cohesion_step(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
+      for (int g = 0; g < Geo::GX; ++g) {
+        lds<4>(ad + kk * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
+        lds<4>(ar + kk * Geo::BX + Geo::row_off(tx, 4 * g), r1 + 4 * g);
       }
-    if (MODE == PALD_ACCUM_COMPENSATED) {
-      // pair (x, z) folds after the y with y mod 4 == fold_phase(i, j):
-      // half of a thread's pairs fold at each of two y in four, spreading
-      // the packed adds over the FMA pipe
+#pragma unroll
+      for (int g = 0; g < Geo::GY; ++g) {
+        lds<Geo::CW>(bd + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), a2 + Geo::CW * g);
+        lds<Geo::CW>(br + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), r2 + Geo::CW * g);
+      }
 #pragma unroll
       for (int i = 0; i < TX; ++i)
 #pragma unroll
-        for (int j = 0; j < TY; ++j)
-          if ((kk % kMergeEvery) == fold_phase(i, j)) fast2sum_fold(hacc[i][j], sacc[i][j]);
+        for (int j = 0; j < TY; ++j) {
+          if (SHORT)
+            cohesion_step_short(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
+          else
+            cohesion_step(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
+        }
+      if (MODE == PALD_ACCUM_COMPENSATED) {
+        // pair (x, z) folds after the y with y mod 4 == fold_phase(i, j)
+        // (k0 and every stage start are multiples of 4): half of a thread's
+        // pairs fold at each of two y in four, spreading the packed adds
+        // over the FMA pipe
+#pragma unroll
+        for (int i = 0; i < TX; ++i)
+#pragma unroll
+          for (int j = 0; j < TY; ++j)
+            if ((k % kMergeEvery) == fold_phase(i, j)) fast2sum_fold(hacc[i][j], sacc[i][j]);
+      }
     }
   }
 }
@@ -264,6 +271,23 @@ __device__ __forceinline__ void cohesion_init(const float* __restrict__ D, int64
     }
 }
 
+// Value of the xz (or zx) lane of a pair: compensated (H - B) + S, or plain
+// S, times 1/(n-1) = ih + il, formed exactly as a two-float value and
+// rounded once.
+template <int MODE>
+__device__ __forceinline__ float cohesion_value(uint64_t h2, uint64_t s2, bool zx, float ih, float il) {
+  float hl, hh, sl, sh;
+  unpack2(h2, hl, hh);
+  unpack2(s2, sl, sh);
+  const float h = zx ? hh : hl, s = zx ? sh : sl;
+  if (MODE == PALD_ACCUM_COMPENSATED) {
+    float p, e;
+    two_sum(__fsub_rn(h, kMergeBias), s, p, e);  // H - B is exact: B is a multiple of H's unit
+    return mul_pair(p, e, ih, il);
+  }
+  return mul_pair(s, 0.f, ih, il);
+}
+
 // Final merge and stores of C[X, Z] (and of C[Z, X] when `mirror`).
 template <class Geo, int MODE>
 __device__ __forceinline__ void cohesion_finish(float* __restrict__ C, int64_t n, int64_t X0, int64_t Z0, int tx,
@@ -272,20 +296,7 @@ __device__ __forceinline__ void cohesion_finish(float* __restrict__ C, int64_t n
                                                 const uint64_t (&hacc)[Geo::TX][Geo::TY]) {
   float ih, il;
   inverse_pair(n - 1, ih, il);
-  // value of the (xz or zx) lane: compensated (H - B) + S, or plain S, times
-  // 1/(n-1), formed exactly as a two-float value and rounded once
-  auto finish = [&](uint64_t h2, uint64_t s2, bool zx) -> float {
-    float hl, hh, sl, sh;
-    unpack2(h2, hl, hh);
-    unpack2(s2, sl, sh);
-    const float h = zx ? hh : hl, s = zx ? sh : sl;
-    if (MODE == PALD_ACCUM_COMPENSATED) {
-      float p, e;
-      two_sum(__fsub_rn(h, kMergeBias), s, p, e);  // H - B is exact: B is a multiple of H's unit
-      return mul_pair(p, e, ih, il);
-    }
-    return mul_pair(s, 0.f, ih, il);
-  };
+  auto finish = [&](uint64_t h2, uint64_t s2, bool zx) -> float { return cohesion_value<MODE>(h2, s2, zx, ih, il); };
 #pragma unroll
   for (int i = 0; i < Geo::TX; ++i) {
     const int64_t x = X0 + Geo::row_off(tx, i);
@@ -401,19 +412,23 @@ struct CohesionTmaSmem {
 
 // Returns false when a wait ran out of time; the CTA then stops early and
 // its outputs are unspecified.  `tie_words` holds tie_map_dims(n).wpp words
-// of shared memory.
+// of shared memory.  With `skip_diag` a diagonal tile leaves out its 4 x 4
+// blocks on the diagonal (the pairs inside the groups of four points), for
+// cohesion_group below to compute: four warps instead of five.
 template <class Geo, int MODE>
 __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const CUtensorMap* tmR,
                                                   const float* __restrict__ D, int64_t n, float* __restrict__ C,
                                                   const uint32_t* __restrict__ tmap, float S, int bi, int bj,
-                                                  bool vec, TmaRing<4, Geo::BK>& ring, uint32_t* tie_words) {
+                                                  bool vec, TmaRing<4, Geo::BK>& ring, uint32_t* tie_words,
+                                                  bool skip_diag = false) {
   constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY, NT = Geo::NT;
   static_assert(Geo::BX == 64 && Geo::BY == 64 && Geo::TPX == 16 && Geo::TPY == 16 && Geo::GX == 1 &&
                     Geo::GY == 1 && Geo::CW == 4,
                 "TMA tiles are 64 x 64 with 4 x 4 pairs per thread");
   cohesion_tile_checks<Geo>();
   int tx, tz;
-  const bool active = tile_block_64(bi, bj, n, threadIdx.x, &tx, &tz);
+  const bool active = tile_block_64(bi, bj, n, threadIdx.x, &tx, &tz, skip_diag);
+  const int64_t X0 = int64_t(bi) * 64;
   const int nstages = static_cast<int>((n + BK - 1) / BK);
 
   if (threadIdx.x == 0) ring.init();
@@ -430,7 +445,7 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
 
   float cv[TX][TY];
   uint64_t sacc[TX][TY], hacc[TX][TY];
-  cohesion_init<Geo>(D, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, tz, S, cv, sacc, hacc);
+  cohesion_init<Geo>(D, n, X0, int64_t(bj) * 64, tx, tz, S, cv, sacc, hacc);
 
   constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
   const CUtensorMap* const maps[4] = {tmD, tmR, tmD, tmR};
@@ -440,21 +455,147 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
       [&](int st, int buf) {
         if (!active) return;
         const int g = st * BK / kTieGroup;
+        const int kend = stage_extent<BK, Geo::UNR>(n, st);
         if ((tie_words[g >> 5] >> (g & 31)) & kGroupMask)
           cohesion_stage<Geo, MODE, false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
-                                           ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc);
+                                           ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, kend);
         else
           cohesion_stage<Geo, MODE, true>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
-                                          ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc);
+                                          ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, kend);
       });
   __syncthreads();
   if (threadIdx.x == 0) ring.inval();
   // off the diagonal, or for an above-diagonal block of a diagonal tile,
   // the block's mirror (the zx lanes) is written too
   if (ok && active)
-    cohesion_finish<Geo, MODE>(C, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, tz, tx != tz || bi != bj, vec, sacc,
-                               hacc);
+    cohesion_finish<Geo, MODE>(C, n, X0, int64_t(bj) * 64, tx, tz, tx != tz || bi != bj, vec, sacc, hacc);
   return ok;
+}
+
+// ---------------------------------------------------------------------------
+// The pairs inside one group of four points x0 .. x0+3 (x0 = 4q), which a
+// diagonal TMA tile with `skip_diag` leaves out: one thread per group,
+// streaming y straight from global memory (the group's four columns of row
+// y are one 16-byte vector).  Only the ten pairs i <= j are formed (pair
+// (j, i) repeats pair (i, j) with the two lanes swapped).  Each lane repeats
+// the tile's operations on its pair in the same order: the same step in the
+// form the tile's stage takes (the tie map's bit of block pair (x0 / 64,
+// x0 / 64) per 32 y), the fold after the same y, the same final merge.  The
+// tile also runs zero-filled y past n; those add +0, and folding the last
+// partial into H leaves H + S, and so the merged value, unchanged: stopping
+// at the first multiple of 4 past n gives the same bits.
+
+__device__ __forceinline__ float comp4(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Row y, columns x0 .. x0+3 of a matrix of order n with row pitch `pitch`
+// (a multiple of 4, 16-byte aligned rows; the columns up to the pitch
+// exist); zeros for y >= n.
+__device__ __forceinline__ float4 group_row(const float* __restrict__ M, int64_t pitch, int64_t n, int64_t y,
+                                            int64_t x0) {
+  if (y >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
+  return __ldg(reinterpret_cast<const float4*>(M + y * pitch + x0));
+}
+
+// One y of the ten pairs, then the folds due after it (y mod 4 == K).
+template <int MODE, bool SHORT, int K>
+__device__ __forceinline__ void cohesion_group_y(const float4& d, const float4& r, float S, const float (&cv)[10],
+                                                 uint64_t (&sacc)[10], uint64_t (&hacc)[10]) {
+#pragma unroll
+  for (int p = 0; p < 10; ++p) {
+    const int i = group_pair_i(p), j = group_pair_j(p);
+    if (SHORT)
+      cohesion_step_short(sacc[p], comp4(d, i), comp4(d, j), S, cv[p], comp4(r, i), comp4(r, j));
+    else
+      cohesion_step(sacc[p], comp4(d, i), comp4(d, j), S, cv[p], comp4(r, i), comp4(r, j));
+  }
+  if (MODE == PALD_ACCUM_COMPENSATED) {
+#pragma unroll
+    for (int p = 0; p < 10; ++p)
+      if (K == fold_phase(group_pair_i(p), group_pair_j(p))) fast2sum_fold(hacc[p], sacc[p]);
+  }
+}
+
+template <int MODE, bool SHORT>
+__device__ __forceinline__ void cohesion_group_4y(const float4 (&d)[4], const float4 (&r)[4], float S,
+                                                  const float (&cv)[10], uint64_t (&sacc)[10],
+                                                  uint64_t (&hacc)[10]) {
+  cohesion_group_y<MODE, SHORT, 0>(d[0], r[0], S, cv, sacc, hacc);
+  cohesion_group_y<MODE, SHORT, 1>(d[1], r[1], S, cv, sacc, hacc);
+  cohesion_group_y<MODE, SHORT, 2>(d[2], r[2], S, cv, sacc, hacc);
+  cohesion_group_y<MODE, SHORT, 3>(d[3], r[3], S, cv, sacc, hacc);
+}
+
+// C of the sixteen pairs of group q.  Dp, Rp: D and R = 1/u with row pitch
+// `pitch` (16-byte aligned rows, finite values in the pad columns); C: row
+// pitch n (vector stores when `vecC`); tmap: the matrix's tie map (null:
+// long form everywhere).
+template <int MODE>
+__device__ __forceinline__ void cohesion_group(const float* __restrict__ Dp, const float* __restrict__ Rp,
+                                               int64_t pitch, int64_t n, int64_t q, float S, float* __restrict__ C,
+                                               bool vecC, const uint32_t* __restrict__ tmap) {
+  const int64_t x0 = 4 * q;
+  float cv[10];
+  uint64_t sacc[10], hacc[10];
+  {
+    float4 row[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) row[i] = group_row(Dp, pitch, n, x0 + i, x0);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) {
+      cv[k] = __fmul_rn(-comp4(row[group_pair_i(k)], group_pair_j(k)), S);  // exact: power of two
+      sacc[k] = pack2(0.f, 0.f);
+      hacc[k] = pack2(kMergeBias, kMergeBias);
+    }
+  }
+  const TieMapDims dm = tie_map_dims(n);
+  const int64_t bx = x0 / kTieBlock;
+  const bool all_long = tmap == nullptr || __ldg(tmap + dm.nb * dm.nb * dm.wpp + bx) != 0u;
+  const uint32_t* trow = tmap + (bx * dm.nb + bx) * dm.wpp;
+  static_assert(kTieGroup % 4 == 0, "tie groups hold whole 4-y steps");
+
+  const int64_t n4 = (n + 3) / 4 * 4;
+  float4 d[4], r[4], dn[4], rn[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    d[k] = group_row(Dp, pitch, n, k, x0);
+    r[k] = group_row(Rp, pitch, n, k, x0);
+  }
+  bool tied = true;
+  for (int64_t y0 = 0; y0 < n4; y0 += 4) {
+    if (y0 % kTieGroup == 0) {
+      const int64_t g = y0 / kTieGroup;
+      tied = all_long || ((__ldg(trow + (g >> 5)) >> (g & 31)) & 1u);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {  // the next four rows, loaded while these are used
+      dn[k] = group_row(Dp, pitch, n, y0 + 4 + k, x0);
+      rn[k] = group_row(Rp, pitch, n, y0 + 4 + k, x0);
+    }
+    if (tied)
+      cohesion_group_4y<MODE, false>(d, r, S, cv, sacc, hacc);
+    else
+      cohesion_group_4y<MODE, true>(d, r, S, cv, sacc, hacc);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      d[k] = dn[k];
+      r[k] = rn[k];
+    }
+  }
+  float ih, il;
+  inverse_pair(n - 1, ih, il);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int p = i <= j ? (i == 0 ? j : (i == 1 ? j + 3 : (i == 2 ? j + 5 : 9)))
+                           : (j == 0 ? i : (j == 1 ? i + 3 : (j == 2 ? i + 5 : 9)));
+      v[j] = cohesion_value<MODE>(hacc[p], sacc[p], i > j, ih, il);
+    }
+    storew<4>(C, n, x0 + i, x0, v, vecC);
+  }
 }
 
 // R[row][col] = 1/u (correctly rounded FP32), 0 on the diagonal and where

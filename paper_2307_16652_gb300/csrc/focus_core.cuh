@@ -157,29 +157,45 @@ __device__ __forceinline__ void focus_init(const float* __restrict__ D, int64_t 
   }
 }
 
+// Valid streamed indices of stage st, rounded up to a whole chunk of CH:
+// the zero-filled rows past n add nothing to either pass, so whole chunks of
+// them are skipped.
+template <int BK, int CH>
+__device__ __forceinline__ int stage_extent(int64_t n, int st) {
+  const int64_t nk = n - static_cast<int64_t>(st) * BK;
+  return nk >= BK ? BK : static_cast<int>((nk + CH - 1) / CH) * CH;
+}
+
 // One pipeline stage (BK consecutive z): as = D[z-stage][X], bs = D[z-stage][Y].
-template <class Geo>
+// The stage runs in chunks of CH z (the first `kend` z, a multiple of CH).
+template <class Geo, int CH = Geo::BK>
 __device__ __forceinline__ void focus_stage(const float* as, const float* bs, int tx, int ty, float scale,
                                             const float (&cst)[Geo::TX][Geo::TY],
-                                            uint64_t (&acc)[Geo::TX][Geo::TY]) {
+                                            uint64_t (&acc)[Geo::TX][Geo::TY], int kend = Geo::BK) {
   constexpr int TX = Geo::TX, TY = Geo::TY;
-#pragma unroll Geo::UNR / 2
-  for (int kk = 0; kk < Geo::BK; kk += 2) {
-    float a0[TX], b0[TY], a1[TX], b1[TY];
+  constexpr int U2 = (CH == Geo::BK ? Geo::UNR : CH) / 2;
+  static_assert(Geo::BK % CH == 0 && CH % 2 == 0, "chunks must tile the stage in pairs of z");
+#pragma unroll 1
+  for (int k0 = 0; k0 < kend; k0 += CH) {
+#pragma unroll U2
+    for (int k = 0; k < CH; k += 2) {
+      const int kk = k0 + k;
+      float a0[TX], b0[TY], a1[TX], b1[TY];
 #pragma unroll
-    for (int g = 0; g < Geo::GX; ++g) {
-      lds<4>(as + kk * Geo::BX + Geo::row_off(tx, 4 * g), a0 + 4 * g);
-      lds<4>(as + (kk + 1) * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
+      for (int g = 0; g < Geo::GX; ++g) {
+        lds<4>(as + kk * Geo::BX + Geo::row_off(tx, 4 * g), a0 + 4 * g);
+        lds<4>(as + (kk + 1) * Geo::BX + Geo::row_off(tx, 4 * g), a1 + 4 * g);
+      }
+#pragma unroll
+      for (int g = 0; g < Geo::GY; ++g) {
+        lds<Geo::CW>(bs + kk * Geo::BY + Geo::col_off(ty, Geo::CW * g), b0 + Geo::CW * g);
+        lds<Geo::CW>(bs + (kk + 1) * Geo::BY + Geo::col_off(ty, Geo::CW * g), b1 + Geo::CW * g);
+      }
+#pragma unroll
+      for (int i = 0; i < TX; ++i)
+#pragma unroll
+        for (int j = 0; j < TY; ++j) focus_step2(acc[i][j], a0[i], b0[j], a1[i], b1[j], scale, cst[i][j]);
     }
-#pragma unroll
-    for (int g = 0; g < Geo::GY; ++g) {
-      lds<Geo::CW>(bs + kk * Geo::BY + Geo::col_off(ty, Geo::CW * g), b0 + Geo::CW * g);
-      lds<Geo::CW>(bs + (kk + 1) * Geo::BY + Geo::col_off(ty, Geo::CW * g), b1 + Geo::CW * g);
-    }
-#pragma unroll
-    for (int i = 0; i < TX; ++i)
-#pragma unroll
-      for (int j = 0; j < TY; ++j) focus_step2(acc[i][j], a0[i], b0[j], a1[i], b1[j], scale, cst[i][j]);
   }
 }
 
@@ -298,41 +314,146 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
   focus_finish<Geo>(U, n, X0, Y0, tx, ty, bi != bj, vec, acc);
 }
 
+// ---------------------------------------------------------------------------
+// Group pairs of a diagonal pass-1 TMA tile.
+//
+// A diagonal 64 x 64 tile of focus_tile_tma with `skip_diag` hands threads
+// only its 4 x 4 blocks strictly above the diagonal (120 blocks: threads
+// 0..119, warps 0..3, one per scheduler).  The pairs (x, z) with
+// x / 4 == z / 4, which its sixteen diagonal blocks would hold, go to the
+// four warps that are left (threads 128..255): ten pairs per group (i <= j;
+// u is symmetric), pair slot p = 10 g + k of group g, slots t - 128 and t for
+// thread t (the second only for threads below 160, so 160 slots in all).
+// Each of those warps carries one or two pairs per lane instead of a block's
+// sixteen, so a diagonal tile costs about half a full one instead of a whole
+// one, and reads only the tile's own panel.  The counts are exact, so the
+// bits are the block code's.  (Pass 2 leaves these pairs to cohesion_group,
+// a kernel of its own: beside pass 2's long unrolled loops the extra
+// shared-memory reads of in-tile group warps cost more than they save.)
+
+// Pair k = 0..9 of a group: (i, j) with i <= j, row by row.
+__host__ __device__ constexpr int group_pair_i(int k) { return k < 4 ? 0 : (k < 7 ? 1 : (k < 9 ? 2 : 3)); }
+__host__ __device__ constexpr int group_pair_j(int k) {
+  return k < 4 ? k : (k < 7 ? k - 3 : (k < 9 ? k - 5 : 3));
+}
+
+constexpr int kGroupThread0 = 128;  // first thread of the group warps
+
+// The (up to two) pairs of thread t on a diagonal tile whose rows are
+// X0 .. X0 + rows - 1 (rows >= 1; the tile's ragged end included).
+struct GroupPairs {
+  int cnt;          // pairs of this thread: 0, 1 or 2
+  int ci[2], cj[2]; // tile columns 4g + i, 4g + j of the pair's points
+  __device__ __forceinline__ GroupPairs(int t, int64_t rows) {
+    const int ax = rows >= 64 ? 16 : static_cast<int>((rows + 3) / 4);  // groups holding rows
+    const int total = 10 * ax;
+    cnt = 0;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int p = t - kGroupThread0 + kGroupThread0 * s;
+      const bool on = t >= kGroupThread0 && p < total;
+      const int g = p / 10, k = p - 10 * (p / 10);
+      ci[s] = on ? 4 * g + group_pair_i(k) : 0;
+      cj[s] = on ? 4 * g + group_pair_j(k) : 0;
+      if (on) cnt = s + 1;
+    }
+  }
+};
+
+// Pass 1, one stage: the group pairs' counts in acc[0][0] and acc[0][1]
+// (the packed counts of z even / odd, as focus_step2 keeps them).  as is
+// the stage's panel D[z-stage][X].
+template <class Geo, int CH>
+__device__ __forceinline__ void focus_group_stage(const float* as, const GroupPairs& gp, float scale,
+                                                  const float (&cst)[Geo::TX][Geo::TY],
+                                                  uint64_t (&acc)[Geo::TX][Geo::TY], int kend) {
+#pragma unroll 1
+  for (int k0 = 0; k0 < kend; k0 += 4) {  // a short loop body, as in cohesion_group_stage
+#pragma unroll
+    for (int k = 0; k < 4; k += 2) {
+      const float* a = as + (k0 + k) * Geo::BX;
+      const float* b = a + Geo::BX;
+      focus_step2(acc[0][0], a[gp.ci[0]], a[gp.cj[0]], b[gp.ci[0]], b[gp.cj[0]], scale, cst[0][0]);
+      if (gp.cnt > 1)
+        focus_step2(acc[0][1], a[gp.ci[1]], a[gp.cj[1]], b[gp.ci[1]], b[gp.cj[1]], scale, cst[0][1]);
+    }
+  }
+}
+
+// Stores u (and 1/u into R when given, recip_entry) of the group pairs,
+// both orders; a[s] is pair s's packed count.
+__device__ __forceinline__ void focus_group_finish(int32_t* __restrict__ U, int64_t n, int64_t X0,
+                                                   const GroupPairs& gp, const uint64_t (&a)[2],
+                                                   float* __restrict__ R, int64_t rpitch) {
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int64_t x = X0 + gp.ci[s], z = X0 + gp.cj[s];
+    if (s < gp.cnt && x < n && z < n) {
+      const int32_t u = static_cast<int32_t>(n) - count_of(a[s]);
+      U[x * n + z] = u;
+      U[z * n + x] = u;
+      if (R) {
+        R[x * rpitch + z] = recip_entry(u, x, z);
+        R[z * rpitch + x] = recip_entry(u, z, x);
+      }
+    }
+  }
+}
+
 // TMA-staged pass-1 tile (64 x 64, see tma_ring.cuh): the X and Y panels of
 // each stage come from the tensor map `tmD` of the n x n matrix (which may
 // be a row-padded copy); thresholds are read from D (row pitch n), U is
 // written with row pitch n, and R = 1/u too when R is given (focus_finish).
-// Returns false when a wait ran out of time.
+// With `skip_diag` a diagonal tile runs its pairs inside the groups of four
+// points on the threads from 128 on (GroupPairs above).  Returns false when
+// a wait ran out of time.
 template <class Geo>
 __device__ __forceinline__ bool focus_tile_tma(const CUtensorMap* tmD, const float* __restrict__ D, int64_t n,
                                                int32_t* __restrict__ U, int bi, int bj, float scale, bool vec,
                                                TmaRing<2, Geo::BK>& ring, float* __restrict__ R = nullptr,
-                                               int64_t rpitch = 0) {
+                                               int64_t rpitch = 0, bool skip_diag = false) {
   static_assert(Geo::BX == 64 && Geo::BY == 64 && Geo::TPX == 16 && Geo::TPY == 16 && Geo::GX == 1 &&
                     Geo::GY == 1 && Geo::CW == 4,
                 "TMA tiles are 64 x 64 with 4 x 4 pairs per thread");
   constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY;
   int tx, ty;
-  const bool active = tile_block_64(bi, bj, n, threadIdx.x, &tx, &ty);
+  const bool active = tile_block_64(bi, bj, n, threadIdx.x, &tx, &ty, skip_diag);
+  const bool grp = skip_diag && bi == bj && threadIdx.x >= kGroupThread0;  // a group-pair thread
+  const int64_t X0 = int64_t(bi) * 64, rows = n - X0;
   const int nstages = static_cast<int>((n + BK - 1) / BK);
+  constexpr int CH = 16;  // the last stage runs only its chunks that hold rows of the matrix
   if (threadIdx.x == 0) ring.init();
   __syncthreads();
   float cst[TX][TY];
   uint64_t acc[TX][TY];
-  focus_init<Geo>(D, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, ty, scale, cst, acc);
+  focus_init<Geo>(D, n, X0, int64_t(bj) * 64, tx, ty, scale, cst, acc);
+  if (grp) {  // the group pairs' thresholds take slots [0][0] and [0][1]
+    const GroupPairs gp(threadIdx.x, rows);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int64_t x = X0 + gp.ci[s], z = X0 + gp.cj[s];
+      cst[0][s] = (s < gp.cnt && x < n && z < n) ? -__ldg(D + x * n + z) * scale : 0.f;
+    }
+  }
   const CUtensorMap* const maps[2] = {tmD, tmD};
   const int cols[2] = {bi * 64, bj * 64};
   const bool ok = tma_pipeline(ring, nstages, [&](int q) { ring.issue(q, maps, cols); },
-                               [&](int, int buf) {
-                                 if (active)
-                                   focus_stage<Geo>(ring.panel(buf, 0), ring.panel(buf, 1), tx, ty, scale, cst, acc);
+                               [&](int st, int buf) {
+                                 const int kend = stage_extent<BK, CH>(n, st);
+                                 if (grp)
+                                   focus_group_stage<Geo, CH>(ring.panel(buf, 0), GroupPairs(threadIdx.x, rows),
+                                                              scale, cst, acc, kend);
+                                 else if (active)
+                                   focus_stage<Geo, CH>(ring.panel(buf, 0), ring.panel(buf, 1), tx, ty, scale, cst,
+                                                        acc, kend);
                                });
   __syncthreads();
   if (threadIdx.x == 0) ring.inval();
   // off the diagonal, or for an above-diagonal block of a diagonal tile,
   // the block's mirror is written too
   if (ok && active)
-    focus_finish<Geo>(U, n, int64_t(bi) * 64, int64_t(bj) * 64, tx, ty, tx != ty || bi != bj, vec, acc, R, rpitch);
+    focus_finish<Geo>(U, n, X0, int64_t(bj) * 64, tx, ty, tx != ty || bi != bj, vec, acc, R, rpitch);
+  if (ok && grp) focus_group_finish(U, n, X0, GroupPairs(threadIdx.x, rows), {acc[0][0], acc[0][1]}, R, rpitch);
   return ok;
 }
 

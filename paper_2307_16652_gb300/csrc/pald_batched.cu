@@ -13,9 +13,14 @@
 // graph and replayed on later calls with the same arguments.
 //
 // Device side: each persistent CTA takes the next work item from a global
-// atomic counter and runs the TMA tile code of the single-matrix kernels on
-// the item's matrix.  A CTA that finds the list exhausted exits; the only
-// waits are the bounded mbarrier waits of the TMA ring.
+// atomic counter (claiming the one after it while the tile runs) and runs
+// the TMA tile code of the single-matrix kernels on the item's matrix.  A
+// CTA that finds the list exhausted exits; the only waits are the bounded
+// mbarrier waits of the TMA ring.  Diagonal tiles run their 4 x 4 blocks
+// above the diagonal on four warps, so they cost about half a full tile; the
+// pairs inside the groups of four points go, in pass 1, to the tile's other
+// four warps (GroupPairs in focus_core.cuh) and, in pass 2, to a kernel with
+// one thread per group after the tiles (cohesion_group in cohesion_core.cuh).
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -42,6 +47,7 @@ constexpr int kTieBlocksPerMatrix = 16;
 constexpr int kMaxGridY = 65535;  // matrices beyond it are strided over blockIdx.y
 constexpr int kMaxBatchedN = 4096;
 constexpr int kTieWordsBatched = ((kMaxBatchedN + kTieGroup - 1) / kTieGroup + 31) / 32;
+constexpr int kGroupThreads = 128;  // groups of four points per CTA of the pass-2 group kernel
 
 // Set by a CTA whose bounded wait gave up (never in normal operation).
 __device__ uint32_t g_batched_faults;
@@ -84,9 +90,16 @@ __global__ void __launch_bounds__(TieSmall::kThreads) batched_prep_kernel(const 
     const PadDesc pd = pads[m];
     const TieMapDims dm = tie_map_dims(md.n);
     uint32_t inv_min = 0u, mx = 0u;
-    for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x)
+    for (int64_t row = blockIdx.x; row < md.n; row += gridDim.x) {
+      // the CTA's next row heads for L2 while this one is hashed (one
+      // prefetch per 128-byte line)
+      const int64_t next = row + gridDim.x;
+      if (next < md.n)
+        for (int64_t c = 32 * static_cast<int64_t>(threadIdx.x); c < md.n; c += 32 * TieSmall::kThreads)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(D + md.off + next * md.n + c));
       tie_map_row<TieSmall>(D + md.off, md.n, row, tmaps + md.tmap_off, dm, sm,
                             PrepVisit{Dp + pd.off_p + row * pd.pitch, &inv_min, &mx});
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       inv_min = max(inv_min, __shfl_xor_sync(0xffffffffu, inv_min, o));
@@ -99,12 +112,28 @@ __global__ void __launch_bounds__(TieSmall::kThreads) batched_prep_kernel(const 
   }
 }
 
-__device__ __forceinline__ int64_t next_item(int* counter, int* slot) {
-  __syncthreads();  // every thread is done with the previous item's shared memory
-  if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
-  __syncthreads();
-  return *slot;
-}
+// Work-list cursor of a persistent CTA: `slot` (shared) holds the current
+// item; thread 0 claims the next one as soon as a tile starts, so the atomic
+// round trip overlaps the tile.
+struct ItemCursor {
+  int* counter;
+  int* slot;
+  int next;
+  __device__ __forceinline__ int64_t first() {
+    if (threadIdx.x == 0) *slot = atomicAdd(counter, 1);
+    __syncthreads();
+    return *slot;
+  }
+  __device__ __forceinline__ void claim_next() {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+  }
+  __device__ __forceinline__ int64_t advance() {
+    __syncthreads();  // every thread has read the slot and is done with the tile's shared memory
+    if (threadIdx.x == 0) *slot = next;
+    __syncthreads();
+    return *slot;
+  }
+};
 
 // maps[2m] is matrix m's padded D, maps[2m + 1] its padded R.
 __global__ void __launch_bounds__(FG::NT, 2) batched_focus_kernel(const float* __restrict__ D, int32_t* __restrict__ U,
@@ -119,15 +148,15 @@ __global__ void __launch_bounds__(FG::NT, 2) batched_focus_kernel(const float* _
   __shared__ int slot;
   TmaRing<2, FG::BK> ring;
   ring.carve(smem);
-  for (;;) {
-    const int64_t it = next_item(counter, &slot);
-    if (it >= n_items) break;
+  ItemCursor cur{counter, &slot, 0};
+  for (int64_t it = cur.first(); it < n_items; it = cur.advance()) {
+    cur.claim_next();
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
     const PadDesc pd = pads[w.matrix];
     const float scale = focus_scale(scans[w.matrix].inv_min_pos_bits);
     if (!focus_tile_tma<FG>(maps + 2 * w.matrix, D + md.off, md.n, U + md.off, w.bi, w.bj, scale, md.n % 4 == 0,
-                            ring, Rp + pd.off_p, pd.pitch)) {
+                            ring, Rp + pd.off_p, pd.pitch, true)) {
       if (threadIdx.x == 0) atomicOr(&g_batched_faults, 1u);
       break;
     }
@@ -147,17 +176,36 @@ __global__ void __launch_bounds__(CG::NT, 2) batched_cohesion_kernel(const float
   __shared__ int slot;
   TmaRing<4, CG::BK> ring;
   uint32_t* tie_words = reinterpret_cast<uint32_t*>(ring.carve(smem));
-  for (;;) {
-    const int64_t it = next_item(counter, &slot);
-    if (it >= n_items) break;
+  ItemCursor cur{counter, &slot, 0};
+  for (int64_t it = cur.first(); it < n_items; it = cur.advance()) {
+    cur.claim_next();
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
     const float S = focus_scale(scans[w.matrix].inv_min_pos_bits);
     if (!cohesion_tile_tma<CG, MODE>(maps + 2 * w.matrix, maps + 2 * w.matrix + 1, D + md.off, md.n, C + md.off,
-                                     tmaps + md.tmap_off, S, w.bi, w.bj, md.n % 4 == 0, ring, tie_words)) {
+                                     tmaps + md.tmap_off, S, w.bi, w.bj, md.n % 4 == 0, ring, tie_words, true)) {
       if (threadIdx.x == 0) atomicOr(&g_batched_faults, 1u);
       break;
     }
+  }
+}
+
+// Pass 2's pairs inside each group of four points, which the diagonal tiles
+// leave out: one thread per group, matrices along blockIdx.y (largest first,
+// `order`), groups along x.  Reads the padded copies of D and R.
+template <int MODE>
+__global__ void __launch_bounds__(kGroupThreads, 3) batched_cohesion_group_kernel(
+    float* __restrict__ C, const float* __restrict__ Dp, const float* __restrict__ Rp,
+    const MatrixDesc* __restrict__ mats, const PadDesc* __restrict__ pads, const ScanResult* __restrict__ scans,
+    const uint32_t* __restrict__ tmaps, const int32_t* __restrict__ order, int count) {
+  for (int k = blockIdx.y; k < count; k += gridDim.y) {
+    const int m = order[k];
+    const MatrixDesc md = mats[m];
+    const int64_t q = int64_t(blockIdx.x) * kGroupThreads + threadIdx.x;
+    if (4 * q >= md.n) continue;
+    const PadDesc pd = pads[m];
+    cohesion_group<MODE>(Dp + pd.off_p, Rp + pd.off_p, pd.pitch, md.n, q, focus_scale(scans[m].inv_min_pos_bits),
+                         C + md.off, md.n % 4 == 0, tmaps + md.tmap_off);
   }
 }
 
@@ -235,10 +283,13 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     for (int bi = 0; bi < T; ++bi)
       for (int bj = bi; bj < T; ++bj) items.push_back(WorkItem{i, bi, bj, 0});
   }
+  int64_t max_n = 0;
+  for (int i = 0; i < count; ++i) max_n = std::max(max_n, ns[i]);
   const size_t o_mats = 0;
   const size_t o_pads = align_up(o_mats + sizeof(MatrixDesc) * count, 256);
   const size_t o_scans = align_up(o_pads + sizeof(PadDesc) * count, 256);
-  const size_t o_items = align_up(o_scans + sizeof(ScanResult) * count, 256);
+  const size_t o_order = align_up(o_scans + sizeof(ScanResult) * count, 256);
+  const size_t o_items = align_up(o_order + sizeof(int32_t) * count, 256);
   const size_t o_counters = align_up(o_items + sizeof(WorkItem) * items.size(), 256);
   const size_t o_tmaps = align_up(o_counters + 256, 256);
   const size_t o_maps = align_up(o_tmaps + sizeof(uint32_t) * static_cast<size_t>(tmap_words), 256);
@@ -254,6 +305,7 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   auto* d_mats = reinterpret_cast<MatrixDesc*>(base + o_mats);
   auto* d_pads = reinterpret_cast<PadDesc*>(base + o_pads);
   auto* d_scans = reinterpret_cast<ScanResult*>(base + o_scans);
+  auto* d_order = reinterpret_cast<int32_t*>(base + o_order);
   auto* d_items = reinterpret_cast<WorkItem*>(base + o_items);
   auto* d_counters = reinterpret_cast<int*>(base + o_counters);
   auto* d_tmaps = reinterpret_cast<uint32_t*>(base + o_tmaps);
@@ -268,7 +320,15 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   }
   if (e == cudaSuccess) e = cudaMemcpy(d_mats, mats.data(), sizeof(MatrixDesc) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_pads, pads.data(), sizeof(PadDesc) * count, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
+  // the pad columns of the padded copies are read (by the pass-2 group
+  // kernel) but never written: zero them once
+  if (e == cudaSuccess) e = cudaMemset(d_dpad, 0, sizeof(float) * static_cast<size_t>(pad_elems));
+  if (e == cudaSuccess) e = cudaMemset(d_rpad, 0, sizeof(float) * static_cast<size_t>(pad_elems));
+  // the uploads above ran on the legacy stream, which need not order the
+  // caller's (possibly non-blocking) stream: finish them first
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpy(d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     destroy_plan(p);
@@ -308,12 +368,18 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
       cudaMemsetAsync(d_tmaps, 0, sizeof(uint32_t) * static_cast<size_t>(tmap_words), cs);
     batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_rpad, d_mats, d_pads, d_scans, d_maps, d_items, n_items,
                                                     d_counters);
-    if (plain)
+    const dim3 ggrid(static_cast<unsigned>((max_n + 4 * kGroupThreads - 1) / (4 * kGroupThreads)), gy);
+    if (plain) {
       batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, csmem, cs>>>(D, C, d_mats, d_scans, d_tmaps, d_maps,
                                                                           d_items, n_items, d_counters + 1);
-    else
+      batched_cohesion_group_kernel<PALD_ACCUM_PLAIN><<<ggrid, kGroupThreads, 0, cs>>>(
+          C, d_dpad, d_rpad, d_mats, d_pads, d_scans, d_tmaps, d_order, count);
+    } else {
       batched_cohesion_kernel<PALD_ACCUM_COMPENSATED><<<gc, CG::NT, csmem, cs>>>(
           D, C, d_mats, d_scans, d_tmaps, d_maps, d_items, n_items, d_counters + 1);
+      batched_cohesion_group_kernel<PALD_ACCUM_COMPENSATED><<<ggrid, kGroupThreads, 0, cs>>>(
+          C, d_dpad, d_rpad, d_mats, d_pads, d_scans, d_tmaps, d_order, count);
+    }
     cudaError_t launch_err = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &p.graph);
     if (e == cudaSuccess && launch_err != cudaSuccess) e = launch_err;

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(Geo::NT, 2)
   TmaRing<2, Geo::BK> ring;
   ring.carve(smem_tma);
   const float scale = focus_scale(scan->inv_min_pos_bits);
-  if (!focus_tile_tma<Geo>(&tmD, D, n, U, bi, bj, scale, true, ring) && threadIdx.x == 0)
+  if (!focus_tile_tma<Geo>(&tmD, D, n, U, bi, bj, scale, true, ring, nullptr, 0, true) && threadIdx.x == 0)
     atomicOr(&g_focus_faults, 1u);
 }
 

@@ -88,9 +88,13 @@ __host__ __device__ __forceinline__ void decode_tile(int64_t t, int64_t T, int H
 // out: on a ragged edge tile the blocks inside the matrix, and on a diagonal
 // tile (X == Z) only the blocks (a, b) with a <= b, since a block below the
 // diagonal repeats, with rows and columns swapped, what its mirror above
-// computes.  Threads without a block only take part in the barriers.
-// Returns whether thread t owns a block.
-__device__ __forceinline__ bool tile_block_64(int bi, int bj, int64_t n, int t, int* a, int* b) {
+// computes.  With `skip_diag` a diagonal tile also leaves out its blocks
+// (a, a): 120 blocks instead of 136, four warps instead of five (their
+// pairs go to the other four warps, GroupPairs in focus_core.cuh).
+// Threads without a block only take part in the barriers.  Returns whether
+// thread t owns a block.
+__host__ __device__ __forceinline__ bool tile_block_64(int bi, int bj, int64_t n, int t, int* a, int* b,
+                                                       bool skip_diag = false) {
   const int64_t rx = n - int64_t(bi) * 64, rz = n - int64_t(bj) * 64;
   const int ax = rx >= 64 ? 16 : static_cast<int>((rx + 3) / 4);  // blocks holding rows of the matrix
   const int az = rz >= 64 ? 16 : static_cast<int>((rz + 3) / 4);
@@ -107,15 +111,27 @@ __device__ __forceinline__ bool tile_block_64(int bi, int bj, int64_t n, int t, 
     *b = t / ax;
     return true;
   }
-  int r = 0;  // upper triangle of the ax x ax blocks, row by row
-  while (r < ax && t >= ax - r) {
-    t -= ax - r;
+  // upper triangle of the ax x ax blocks, row by row; row r holds blocks
+  // (r, r + d) .. (r, ax - 1)
+  const int d = skip_diag ? 1 : 0;
+  int r = 0;
+  while (r < ax && t >= ax - r - d) {
+    t -= ax - r - d;
     ++r;
   }
   if (r == ax) return false;
   *a = r;
-  *b = r + t;
+  *b = r + d + t;
   return true;
+}
+
+// Number of blocks tile_block_64 hands out for tile (bi, bj).
+__host__ __device__ __forceinline__ int tile_blocks_64(int bi, int bj, int64_t n, bool skip_diag) {
+  const int64_t rx = n - int64_t(bi) * 64, rz = n - int64_t(bj) * 64;
+  const int ax = rx >= 64 ? 16 : static_cast<int>((rx + 3) / 4);
+  const int az = rz >= 64 ? 16 : static_cast<int>((rz + 3) / 4);
+  if (bi != bj) return ax * az;
+  return skip_diag ? ax * (ax - 1) / 2 : ax * (ax + 1) / 2;
 }
 
 }  // namespace pald
