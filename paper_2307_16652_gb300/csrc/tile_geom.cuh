@@ -93,7 +93,7 @@ __host__ __device__ __forceinline__ void decode_tile(int64_t t, int64_t T, int H
 // pairs go to the other four warps, GroupPairs in focus_core.cuh).
 // Threads without a block only take part in the barriers.  Returns whether
 // thread t owns a block.
-__host__ __device__ __forceinline__ bool tile_block_64(int bi, int bj, int64_t n, int t, int* a, int* b,
+__device__ __forceinline__ bool tile_block_64(int bi, int bj, int64_t n, int t, int* a, int* b,
                                                        bool skip_diag = false) {
   const int64_t rx = n - int64_t(bi) * 64, rz = n - int64_t(bj) * 64;
   const int ax = rx >= 64 ? 16 : static_cast<int>((rx + 3) / 4);  // blocks holding rows of the matrix
@@ -123,15 +123,6 @@ __host__ __device__ __forceinline__ bool tile_block_64(int bi, int bj, int64_t n
   *a = r;
   *b = r + d + t;
   return true;
-}
-
-// Number of blocks tile_block_64 hands out for tile (bi, bj).
-__host__ __device__ __forceinline__ int tile_blocks_64(int bi, int bj, int64_t n, bool skip_diag) {
-  const int64_t rx = n - int64_t(bi) * 64, rz = n - int64_t(bj) * 64;
-  const int ax = rx >= 64 ? 16 : static_cast<int>((rx + 3) / 4);
-  const int az = rz >= 64 ? 16 : static_cast<int>((rz + 3) / 4);
-  if (bi != bj) return ax * az;
-  return skip_diag ? ax * (ax - 1) / 2 : ax * (ax + 1) / 2;
 }
 
 }  // namespace pald
