@@ -125,10 +125,11 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
  *   U         device int32, same layout as D; receives u for every matrix.
  *   C         device FP32, same layout as D; receives C for every matrix.
  * The first call for a given (count, n, off, D, U, C, opts) builds a work
- * plan and a CUDA graph (host work, and it synchronises `stream`); later calls
- * with the same arguments only launch the graph.  A plan holds device memory
- * of about twice the packed D (row-padded copies of D and of R = 1/u, whose
- * 16-byte row pitch the TMA copies need) until pald_release() frees it.
+ * plan and a CUDA graph (host work; it synchronises `stream` and then the
+ * device, once its uploads are queued); later calls with the same arguments
+ * only launch the graph.  A plan holds device memory of about twice the
+ * packed D (row-padded copies of D and of R = 1/u, whose 16-byte row pitch
+ * the TMA copies need) until pald_release() frees it.
  * Errors: INVALID_ARG (bad count, n_i, misaligned or overlapping offsets);
  * validation errors; CUDA; NO_MEMORY.
  */
