@@ -255,3 +255,81 @@ def planted_tie_matrix(rng: np.random.Generator, n: int, ties: int, dim: int = 3
         x, y, z = rng.choice(n, size=3, replace=False)
         d[x, z] = d[z, x] = d[x, y]
     return d
+
+
+# ----------------------------------------------------------------------------
+# graph distances: stand-in for the SNAP collaboration networks (Sec. 7)
+# ----------------------------------------------------------------------------
+#
+# The paper's scaling study runs PaLD on all-pairs shortest-path distances of
+# three co-authorship networks (5,242 to 23,133 authors).  Those files are not
+# available; this recipe grows a graph of the same kind: paper i (one per
+# author) joins a team of 2..5 distinct authors into a clique: author i and
+# co-authors chosen with preferential attachment (probability proportional to
+# 1 + the papers they already have).  Each component other than the largest
+# is then tied to a random author of the largest by one edge, so every
+# distance is finite and the diameter stays small.  d_ij is the hop count (an
+# integer, exact in FP32); the matrices are very tie-heavy.
+
+GRAPH_CONFIG = len(WORKLOADS) + 1  # seed config of the graph workloads ("graph-<n>")
+
+
+def collaboration_edges(rng: np.random.Generator, n: int, team_lo: int = 2, team_hi: int = 5) -> np.ndarray:
+    """Undirected edges (m x 2, u < v) of a connected co-authorship graph on n >= 2 authors."""
+    if n < 2:
+        raise ValueError("a graph workload needs n >= 2")
+    pool = list(range(n))  # author a appears 1 + (papers of a) times
+    edges = set()
+    for lead in range(n):
+        k = int(rng.integers(team_lo, min(team_hi, n) + 1))
+        team = {lead}
+        while len(team) < k:
+            team.add(pool[int(rng.integers(len(pool)))])
+        members = sorted(team)
+        for i, a in enumerate(members):
+            for b in members[i + 1:]:
+                edges.add((a, b))
+        pool.extend(members)
+    e = np.array(sorted(edges), dtype=np.int64).reshape(-1, 2)
+    # tie every other component to a random author of the largest one
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+
+    adj = coo_matrix((np.ones(len(e)), (e[:, 0], e[:, 1])), shape=(n, n))
+    ncomp, labels = connected_components(adj, directed=False)
+    if ncomp > 1:
+        big = int(np.argmax(np.bincount(labels)))
+        in_big = np.flatnonzero(labels == big)
+        links = []
+        for c in range(ncomp):
+            if c != big:
+                a = int(np.flatnonzero(labels == c)[0])
+                b = int(in_big[int(rng.integers(len(in_big)))])
+                links.append((min(a, b), max(a, b)))
+        e = np.concatenate([e, np.array(links, dtype=np.int64)])
+    return e
+
+
+def hop_distances_fp32(n: int, edges: np.ndarray, block: int = 1024) -> np.ndarray:
+    """All-pairs hop counts of the undirected graph (breadth-first search from
+    every vertex, a block of sources at a time) as an FP32 n x n matrix; the
+    graph must be connected."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import shortest_path
+
+    adj = csr_matrix((np.ones(len(edges)), (edges[:, 0], edges[:, 1])), shape=(n, n))
+    adj = adj + adj.T
+    D = np.empty((n, n), np.float32)
+    for r0 in range(0, n, block):
+        rows = np.arange(r0, min(n, r0 + block))
+        d = shortest_path(adj, method="D", directed=False, unweighted=True, indices=rows)
+        if not np.all(np.isfinite(d)):
+            raise ValueError("the graph is not connected")
+        D[rows] = d.astype(np.float32)
+    np.fill_diagonal(D, 0.0)
+    return D
+
+
+def graph_matrix(n: int, index: int = 0) -> np.ndarray:
+    """Hop-distance matrix of the seeded collaboration graph on n authors."""
+    return hop_distances_fp32(n, collaboration_edges(rng_for(GRAPH_CONFIG, index), n))
