@@ -215,6 +215,13 @@ def oracle_rows_rate(D_host, n: int, k: int, seed: int):
     return value, dt, cores
 
 
+def workload_config(args, n: int, world: int) -> dict:
+    """The `config` of both arms' JSON lines (the same keys and values)."""
+    return {"workload": args.workload, "n": n, "accum_mode": "compensated", "schedule": "auto",
+            "l2": "inputs larger than L2 (D is %.1f GB), no flush" % (4 * n * n / 1e9),
+            "parallelism": f"replicas x{world} (independent matrices)"}
+
+
 # ---------------------------------------------------------------------------
 # our arm
 
@@ -290,9 +297,7 @@ def run_ours(args, rank, world, local):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": args.workload, "n": n, "accum_mode": "compensated", "schedule": "auto",
-                      "l2": "inputs larger than L2 (D is %.1f GB), no flush" % (4 * n * n / 1e9),
-                      "parallelism": f"replicas x{world} (independent matrices)"},
+           "config": workload_config(args, n, world),
            "per_pass": per_pass, "roofline": roofline, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
            "clocks": clk}
 
@@ -314,7 +319,8 @@ def run_ours(args, rank, world, local):
             ts.append(time.perf_counter() - t0)
         t = statistics.mean(ts)
         out["e2e"] = {"value": 2.0 * triplets(n) / t, "unit": UNIT, "h2d_bytes_per_step": 4 * n * n,
-                      "d2h_bytes_per_step": 8 * n * n, "steps": e2e_steps, "api": "pald_host"}
+                      "d2h_bytes_per_step": 8 * n * n, "steps": e2e_steps, "api": "pald_host",
+                      "s_per_step": [round(x, 3) for x in ts]}
     if rank == 0 and not args.no_cpu_baseline:
         if D_host is None:
             D_host = D.cpu()
@@ -411,7 +417,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": n},
+            "config": workload_config(args, n, world),
             "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -424,7 +430,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="paper-65536")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=3,
+                    help="pald_host calls timed for the end-to-end number (at most --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--batched-count", type=int, default=2000)
@@ -432,11 +439,16 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")
-    import __graft_entry__
-
     rank, world, local = dist_setup(args)
     if rank == 0 or world == 1:
-        __graft_entry__.build()
+        if args.impl == "reference":
+            import oracle  # the reference arm builds and loads the oracle only
+
+            oracle.build()
+        else:
+            import __graft_entry__
+
+            __graft_entry__.build()
     barrier(world)
     if args.impl == "reference":
         out = run_reference(args, rank, world)

@@ -129,7 +129,15 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
  * device, once its uploads are queued); later calls with the same arguments
  * only launch the graph.  A plan holds device memory of about twice the
  * packed D (row-padded copies of D and of R = 1/u, whose 16-byte row pitch
- * the TMA copies need) until pald_release() frees it.
+ * the TMA copies need) until pald_release() frees it.  At most 16 plans are
+ * kept: building a 17th first frees the least recently used one (after its
+ * last replay has finished).  The cache is keyed on the buffer addresses, so
+ * callers should reuse their D, U and C buffers between calls.
+ * Replays of one plan share its scratch; each replay waits (on the GPU) for
+ * the previous replay of the same plan, whatever stream either was issued
+ * on, so overlapping calls with the same arguments are safe.  Inside a
+ * stream capture that wait is left out and the caller's graph must order
+ * such calls.
  * Errors: INVALID_ARG (bad count, n_i, misaligned or overlapping offsets);
  * validation errors; CUDA; NO_MEMORY.
  */
@@ -233,6 +241,20 @@ int64_t pald_tie_map_words(int64_t n);
  */
 pald_status pald_check_faults(pald_stream_t stream);
 
+/*
+ * pald_test_bounded_wait - diagnostic for the bounded device-side waits (the
+ * paper has no counterpart).  Launches on `stream` one CTA that runs the
+ * TMA pipeline of the pass kernels with no copy ever issued, so its first
+ * mbarrier wait gives up after `limit_ns` nanoseconds; the CTA then takes the
+ * same give-up path as a pass kernel whose copy never completed and records
+ * the fault word that pald_check_faults reports.  The kernel ends after about
+ * three limits; nothing faults or hangs.  Afterwards pald_check_faults
+ * returns PALD_ERR_TIMEOUT once (and clears the record).
+ *   limit_ns  1000 <= limit_ns <= 2e9.
+ * Errors: INVALID_ARG (limit out of range); CUDA.
+ */
+pald_status pald_test_bounded_wait(int64_t limit_ns, pald_stream_t stream);
+
 /* Number of built-in tile schedules and the name of schedule `id` (static
  * string, or NULL if id is out of range).  Used by the autotuner. */
 int32_t pald_schedule_count(void);
@@ -247,8 +269,8 @@ int32_t pald_last_cuda_error(void);
 /* Library version, major*10000 + minor*100 + patch. */
 int32_t pald_version(void);
 
-/* Frees the cached batched plans and graphs of every device.  Must not be
- * called while a batched graph is still running. */
+/* Frees the cached batched plans and graphs of every device, after waiting
+ * for each plan's last replay to finish. */
 void pald_release(void);
 
 #ifdef __cplusplus

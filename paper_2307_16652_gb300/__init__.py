@@ -33,6 +33,7 @@ from .binding import (  # noqa: F401
     pald_schedule_name,
     pald_status_string,
     pald_strong_ties,
+    pald_test_bounded_wait,
     pald_tie_map,
     pald_tie_map_words,
     pald_validate,
@@ -42,7 +43,7 @@ from .binding import (  # noqa: F401
 __all__ = [
     "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PALD_FLAG_IGNORE_TIES", "PaldError", "lib", "library_path", "pald_check_faults",
     "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_local_depth",
-    "pald_release", "pald_strong_ties",
+    "pald_release", "pald_strong_ties", "pald_test_bounded_wait",
     "pald_schedule_count", "pald_schedule_name", "pald_status_string", "pald_tie_map", "pald_tie_map_words",
     "pald_validate", "pald_version",
 ]

@@ -68,12 +68,14 @@ def _lib() -> ctypes.CDLL:
         h.pald_validate.argtypes = [vp, i64, vp]
         h.pald_tie_map.argtypes = [vp, i64, vp, vp]
         h.pald_check_faults.argtypes = [vp]
+        h.pald_test_bounded_wait.argtypes = [i64, vp]
         h.pald_local_depth.argtypes = [vp, i64, vp, vp]
         h.pald_strong_ties.argtypes = [vp, i64, ctypes.c_float, vp, vp]
         h.pald_tie_map_words.argtypes = [i64]
         h.pald_tie_map_words.restype = i64
         for f in (h.pald_focus, h.pald_cohesion, h.pald_cohesion_noalloc, h.pald_batched, h.pald_host,
-                  h.pald_validate, h.pald_tie_map, h.pald_check_faults, h.pald_local_depth, h.pald_strong_ties):
+                  h.pald_validate, h.pald_tie_map, h.pald_check_faults, h.pald_local_depth, h.pald_strong_ties,
+                  h.pald_test_bounded_wait):
             f.restype = ctypes.c_int
         h.pald_status_string.argtypes = [ctypes.c_int]
         h.pald_status_string.restype = ctypes.c_char_p
@@ -269,6 +271,12 @@ def pald_tie_map(D, *, stream=None):
 def pald_check_faults(*, stream=None) -> int:
     """Synchronise and return 0, or 7 (PALD_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
     return _lib().pald_check_faults(_stream_ptr(stream))
+
+
+def pald_test_bounded_wait(limit_ns: int, *, stream=None) -> None:
+    """Diagnostic: launch one CTA whose bounded waits give up after limit_ns
+    (pald_check_faults then reports PALD_ERR_TIMEOUT once)."""
+    _raise(_lib().pald_test_bounded_wait(int(limit_ns), _stream_ptr(stream)), "pald_test_bounded_wait")
 
 
 def pald_schedule_count() -> int:

@@ -4,6 +4,9 @@
 // dispatch; the arithmetic of both passes lives in the kernels.
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "pald_internal.cuh"
 #include "schedules.cuh"
@@ -31,6 +34,21 @@ pald_opts opts_or_default(const pald_opts* o) {
 }
 
 constexpr int64_t kMaxN = int64_t(1) << 20;
+
+cudaError_t smem_opt_in(const void* fn, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> bytes opted in
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(fn, dev);
+  const auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[key] = bytes;
+  return e;
+}
 
 // Maps a scan result (already on the host) to a status.
 pald_status status_from_scan(const ScanResult& r) {
@@ -200,6 +218,12 @@ pald_status pald_check_faults(pald_stream_t stream) {
   if (e == cudaSuccess) e = take_batched_faults(&f3, s);
   if (e != cudaSuccess) return cuda_fail(e);
   return (f1 | f2 | f3) ? PALD_ERR_TIMEOUT : PALD_OK;
+}
+
+pald_status pald_test_bounded_wait(int64_t limit_ns, pald_stream_t stream) {
+  if (limit_ns < 1000 || limit_ns > static_cast<int64_t>(kWaitLimitNs)) return PALD_ERR_INVALID_ARG;
+  const cudaError_t e = launch_wait_selftest(static_cast<uint64_t>(limit_ns), reinterpret_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? PALD_OK : cuda_fail(e);
 }
 
 int32_t pald_schedule_count(void) { return kScheduleCount; }

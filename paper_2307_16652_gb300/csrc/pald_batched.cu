@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kGroupThreads, 3) batched_cohesion_group_kerne
 
 int resident_ctas(const void* fn, int threads, int smem) {
   int per = 1;
-  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+  if (smem_opt_in(fn, smem) != cudaSuccess) return 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1) per = 1;
   return sm_count() * per;
 }
@@ -226,8 +226,13 @@ struct Plan {
   void* dev_mem = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;  // recorded after each replay: the next replay of this plan waits on it
+  uint64_t last_use = 0;       // for least-recently-used eviction
   int device = 0;
 };
+
+// Plans kept at once; building one more frees the least recently used.
+constexpr size_t kMaxPlans = 16;
 
 struct PlanKey {
   std::vector<int64_t> words;
@@ -248,10 +253,15 @@ std::mutex g_plan_mu;
 std::unordered_map<PlanKey, Plan, PlanKeyHash>* g_plans = nullptr;
 cudaStream_t g_capture_stream[64] = {};
 
+// Waits for the plan's last replay, then frees everything it holds.
 void destroy_plan(Plan& p) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(p.device);
+  if (p.done) {
+    cudaEventSynchronize(p.done);
+    cudaEventDestroy(p.done);
+  }
   if (p.exec) cudaGraphExecDestroy(p.exec);
   if (p.graph) cudaGraphDestroy(p.graph);
   if (p.dev_mem) cudaFree(p.dev_mem);
@@ -302,8 +312,13 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
 
   Plan p;
   p.device = device;
-  cudaError_t e = cudaMalloc(&p.dev_mem, total);
+  cudaError_t e = cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming);
   if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaMalloc(&p.dev_mem, total);
+  if (e != cudaSuccess) {
+    destroy_plan(p);
+    return cuda_fail(e);
+  }
   char* base = static_cast<char*>(p.dev_mem);
   auto* d_mats = reinterpret_cast<MatrixDesc*>(base + o_mats);
   auto* d_pads = reinterpret_cast<PadDesc*>(base + o_pads);
@@ -460,23 +475,38 @@ pald_status pald_batched(int32_t count, const int64_t* n_host, const int64_t* of
     key.words.push_back(off_host[i]);
   }
 
-  cudaGraphExec_t exec = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_plan_mu);
-    if (!g_plans) g_plans = new std::unordered_map<PlanKey, Plan, PlanKeyHash>();
-    auto it = g_plans->find(key);
-    if (it == g_plans->end()) {
-      // the plan's graph reads D and writes U, C: order it after the caller's work
-      if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
-      Plan p;
-      pald_status st = build_plan(count, n_host, off_host, D, U, C, o, device, &p);
-      if (st != PALD_OK) return st;
-      it = g_plans->emplace(std::move(key), p).first;
+  // The lock is held until the replay is queued, so pald_release or an
+  // eviction on another thread cannot free the graph in between.
+  std::lock_guard<std::mutex> lock(g_plan_mu);
+  if (!g_plans) g_plans = new std::unordered_map<PlanKey, Plan, PlanKeyHash>();
+  static uint64_t tick = 0;
+  auto it = g_plans->find(key);
+  if (it == g_plans->end()) {
+    // the plan's graph reads D and writes U, C: order it after the caller's work
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e);
+    if (g_plans->size() >= kMaxPlans) {  // free the least recently used plan
+      auto lru = g_plans->begin();
+      for (auto j = g_plans->begin(); j != g_plans->end(); ++j)
+        if (j->second.last_use < lru->second.last_use) lru = j;
+      destroy_plan(lru->second);
+      g_plans->erase(lru);
     }
-    exec = it->second.exec;
+    Plan p;
+    pald_status st = build_plan(count, n_host, off_host, D, U, C, o, device, &p);
+    if (st != PALD_OK) return st;
+    it = g_plans->emplace(std::move(key), p).first;
   }
-  e = cudaGraphLaunch(exec, s);
-  if (e != cudaSuccess) return cuda_fail(e);
+  Plan& plan = it->second;
+  plan.last_use = ++tick;
+  // Every replay of a plan shares its scratch (work counters, padded copies,
+  // tie maps): a replay on another stream first waits for the previous one.
+  // Under stream capture the caller's graph orders its own nodes instead.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return cuda_fail(e);
+  const bool capturing = cap != cudaStreamCaptureStatusNone;
+  if (!capturing && (e = cudaStreamWaitEvent(s, plan.done, 0)) != cudaSuccess) return cuda_fail(e);
+  if ((e = cudaGraphLaunch(plan.exec, s)) != cudaSuccess) return cuda_fail(e);
+  if (!capturing && (e = cudaEventRecord(plan.done, s)) != cudaSuccess) return cuda_fail(e);
   return PALD_OK;
 }
 

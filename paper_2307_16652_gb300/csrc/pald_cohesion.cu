@@ -35,13 +35,8 @@ cudaError_t launch_t(const float* D, const float* R, int64_t n, float* C, const 
   const int64_t ctas = T * (T + 1) / 2 * Geo::H;
   if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
   const int smem = CohesionSmem<Geo>::FLOATS * static_cast<int>(sizeof(float));
-  static bool attr_set = false;  // idempotent: racing setters write the same value
-  if (!attr_set) {
-    cudaError_t e =
-        cudaFuncSetAttribute(cohesion_kernel<Geo, MODE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  const cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(cohesion_kernel<Geo, MODE, MINB>), smem);
+  if (e != cudaSuccess) return e;
   cohesion_kernel<Geo, MODE, MINB><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(D, R, n, C, tmap, scan, T);
   return cudaGetLastError();
 }
@@ -65,6 +60,26 @@ __global__ void __launch_bounds__(CohesionS7::NT, 2)
     atomicOr(&g_cohesion_faults, 1u);
 }
 
+// Self-test of the bounded waits: one CTA runs the TMA pipeline of the pass
+// kernels over a few stages whose copies are never issued, so nothing ever
+// arrives on the ring's barriers.  Its first wait gives up after `limit_ns`,
+// every thread leaves the loop, thread 0 waits (bounded again) for the copies
+// it would have had in flight, and the CTA records the fault word exactly as
+// a pass-2 kernel does.  Nothing faults or hangs: the kernel ends after
+// about three limits.
+__global__ void __launch_bounds__(128) wait_selftest_kernel(uint64_t limit_ns) {
+  __shared__ __align__(128) float smem_ring[TmaRing<1, 16>::BYTES / 4 + 32];
+  TmaRing<1, 16> ring;
+  ring.limit_ns = limit_ns;
+  ring.carve(smem_ring);
+  if (threadIdx.x == 0) ring.init();
+  __syncthreads();
+  const bool ok = tma_pipeline(ring, kTmaStages + 1, [](int) {}, [](int, int) {});
+  __syncthreads();
+  if (threadIdx.x == 0) ring.inval();
+  if (!ok && threadIdx.x == 0) atomicOr(&g_cohesion_faults, 1u);
+}
+
 // The TMA path needs the row pitch and the base addresses 16-byte aligned.
 bool tma_ok(const float* D, const float* R, const float* C, int64_t n) {
   return n >= 64 && n % 4 == 0 && reinterpret_cast<uintptr_t>(D) % 16 == 0 &&
@@ -83,13 +98,8 @@ cudaError_t launch_tma(const float* D, const float* R, int64_t n, float* C, cons
   if (e == cudaSuccess) e = encode_panel_map(&mR, R, n, n, Geo::BK);
   if (e != cudaSuccess) return e;
   const int smem = CohesionTmaSmem<Geo>::bytes(n);  // TMA ring + tie words
-  static bool attr_set = false;  // idempotent: racing setters write the same value
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(cohesion_tma_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             CohesionTmaSmem<Geo>::MAX_BYTES);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  e = smem_opt_in(reinterpret_cast<const void*>(cohesion_tma_kernel<MODE>), CohesionTmaSmem<Geo>::MAX_BYTES);
+  if (e != cudaSuccess) return e;
   cohesion_tma_kernel<MODE><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(mD, mR, D, n, C, tmap, scan, T);
   return cudaGetLastError();
 }
@@ -118,6 +128,11 @@ cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_
   const int64_t cap = int64_t(sm_count()) * 16;
   const int64_t grid = n < cap ? n : cap;
   reciprocal_kernel<<<static_cast<unsigned>(grid), 256, 0, s>>>(U, R, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 128, 0, s>>>(limit_ns);
   return cudaGetLastError();
 }
 

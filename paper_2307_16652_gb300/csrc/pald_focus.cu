@@ -51,12 +51,7 @@ cudaError_t launch_tma(const float* D, int64_t n, int32_t* U, const ScanResult* 
   cudaError_t e = encode_panel_map(&mD, D, n, n, Geo::BK);
   if (e != cudaSuccess) return e;
   const int smem = TmaRing<2, Geo::BK>::BYTES + 128;
-  static bool attr_set = false;  // idempotent: racing setters write the same value
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(focus_tma_kernel<Geo>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  if ((e = smem_opt_in(reinterpret_cast<const void*>(focus_tma_kernel<Geo>), smem)) != cudaSuccess) return e;
   focus_tma_kernel<Geo><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(mD, D, n, U, scan, T);
   return cudaGetLastError();
 }
@@ -67,12 +62,8 @@ cudaError_t launch_t(const float* D, int64_t n, int32_t* U, const ScanResult* sc
   const int64_t ctas = T * (T + 1) / 2 * Geo::H;
   if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
   const int smem = FocusSmem<Geo>::FLOATS * static_cast<int>(sizeof(float));
-  static bool attr_set = false;  // idempotent: racing setters write the same value
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(focus_kernel<Geo, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  const cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(focus_kernel<Geo, MINB>), smem);
+  if (e != cudaSuccess) return e;
   focus_kernel<Geo, MINB><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(D, n, U, scan, T);
   return cudaGetLastError();
 }

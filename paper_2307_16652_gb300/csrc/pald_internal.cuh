@@ -111,11 +111,11 @@ __device__ __forceinline__ uint64_t global_ns() {
 // and reports a fault instead of hanging the GPU.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > kWaitLimitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
 // 2-D tensor copy global -> shared of one box at coordinates (x = column,
@@ -188,6 +188,11 @@ __host__ __device__ __forceinline__ int64_t tie_map_words(int64_t n) {
 // ---------------------------------------------------------------------------
 // Host-side launchers (defined in the .cu files).
 
+// Opts kernel `fn` in to `bytes` of dynamic shared memory on the CURRENT
+// device (the attribute is per device), once per (kernel, device) and size;
+// thread-safe.
+cudaError_t smem_opt_in(const void* fn, int bytes);
+
 cudaError_t launch_scan(const float* D, int64_t n, ScanResult* out, bool validate, cudaStream_t s);
 cudaError_t launch_focus(const float* D, int64_t n, int32_t* U, const ScanResult* scan, int schedule,
                          cudaStream_t s);
@@ -203,6 +208,9 @@ cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C,
 cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s);
 cudaError_t take_focus_faults(uint32_t* out, cudaStream_t s);
 cudaError_t take_batched_faults(uint32_t* out, cudaStream_t s);
+// One CTA whose bounded waits run out after limit_ns (the give-up path of
+// the TMA pipeline); it records the pass-2 fault word.
+cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t s);
 // Tensor map of an n x n FP32 row-major matrix stored with row pitch `pitch`
 // elements (a multiple of 4), with boxes of `rows` x 64.
 cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int64_t pitch, int rows);

@@ -21,13 +21,8 @@ cudaError_t launch_tie_map(const float* D, int64_t n, uint32_t* map, cudaStream_
   const TieMapDims dm = tie_map_dims(n);
   cudaError_t e = cudaMemsetAsync(map, 0, static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t), s);
   if (e != cudaSuccess) return e;
-  static bool attr_set = false;  // idempotent: racing setters write the same value
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(tie_map_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(sizeof(TieLarge::Smem)));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  e = smem_opt_in(reinterpret_cast<const void*>(tie_map_kernel), static_cast<int>(sizeof(TieLarge::Smem)));
+  if (e != cudaSuccess) return e;
   const int64_t cap = sm_count();
   const int64_t grid = n < cap ? n : cap;
   tie_map_kernel<<<static_cast<unsigned>(grid), TieLarge::kThreads, sizeof(TieLarge::Smem), s>>>(D, n, map, dm);

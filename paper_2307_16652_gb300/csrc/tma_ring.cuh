@@ -26,6 +26,7 @@ struct TmaRing {
 
   float* panels;   // [kTmaStages][P][BK][64], 128-byte aligned
   uint64_t* bars;  // [kTmaStages]
+  uint64_t limit_ns = kWaitLimitNs;  // how long a wait may take before it gives up
 
   // Places the ring at the first 128-byte boundary of `smem` (a shared
   // array; offsets keep the compiler on shared-memory loads).  Returns the
@@ -59,7 +60,8 @@ struct TmaRing {
     for (int k = 0; k < P; ++k) tma_load_2d(smem_u32(panel(buf, k)), maps[k], cols[k], q * BK, bar);
   }
   __device__ __forceinline__ bool wait(int st) const {
-    return mbar_wait_bounded(smem_u32(bars + st % kTmaStages), static_cast<uint32_t>((st / kTmaStages) & 1));
+    return mbar_wait_bounded(smem_u32(bars + st % kTmaStages), static_cast<uint32_t>((st / kTmaStages) & 1),
+                             limit_ns);
   }
 };
 
