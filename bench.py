@@ -332,6 +332,70 @@ def run_ours(args, rank, world, local):
                                          f"({dt:.1f} s), scaled by n/{k}"}
     if rank == 0 and not args.no_batched:
         out["batched"] = run_batched_compare(args)
+    if rank == 0 and not args.no_extras:
+        out["other_workloads"] = run_other_workloads(props, (clk or {}).get("sm_max_mhz") or 2070.0)
+    return out
+
+
+def run_other_workloads(props, sm_max):
+    """Per-pass rates on the other single-matrix configs: tie-heavy-4096 (a
+    tie in nearly every 32-y stage: pass 2 runs its 8-slot long form
+    throughout) and precision-16384, plus the pairwise strip variant on the
+    paper recipe at n = 8192 (u never stored)."""
+    import torch
+
+    import paper_2307_16652_gb300 as pald
+    from paper_2307_16652_gb300 import inputs
+
+    stream = torch.cuda.current_stream()
+    peak_ops = props.multi_processor_count * LANES_PER_SM_CLK * sm_max * 1e6
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    for wl, reps in ((inputs.TIE_HEAVY_4096, 5), (inputs.PRECISION_16384, 2)):
+        D = make_matrix(wl)
+        n = D.shape[0]
+        U = torch.empty((n, n), dtype=torch.int32, device="cuda")
+        C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+        T = triplets(n)
+        rec = {"n": n}
+        for name, fn in (("focus", lambda: pald.pald_focus(D, U)), ("cohesion", lambda: pald.pald_cohesion(D, U, C))):
+            ms = timed(fn, reps)
+            rec[name] = {"ms": round(ms, 3), "triplets_per_s": T / (ms / 1e3),
+                         "frac_of_issue_peak": OPS_PER_TRIPLET[name] * T / (ms / 1e3) / peak_ops}
+        words = pald.pald_tie_map_words(n)
+        tmap = pald.pald_tie_map(D)
+        nb = -(-n // 64)
+        import numpy as np
+
+        cells = tmap[:words - nb].cpu().numpy().view(np.uint8)
+        marked = int(np.unpackbits(cells).sum())
+        dirty = int((tmap[words - nb:] != 0).sum())
+        rec["tie_map"] = {"marked_bits": marked, "dirty_blocks": dirty, "blocks": nb}
+        out[wl] = rec
+        del D, U, C
+        torch.cuda.empty_cache()
+    n = 8192
+    D = inputs.euclidean_fp32_torch(inputs.paper_points(n), "cuda")
+    C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    ms = timed(lambda: pald.pald_pairwise(D, C), 2)
+    out["pairwise-paper-8192"] = {"n": n, "ms_both_passes": round(ms, 3),
+                                  "triplets_per_s_per_pass": 2 * triplets(n) / (ms / 1e3) / 2,
+                                  "scratch_bytes": pald.pald_pairwise_scratch_bytes(n),
+                                  "note": "u never stored; every pair's u counted in both orientations"}
+    del D, C
+    torch.cuda.empty_cache()
     return out
 
 
@@ -434,6 +498,7 @@ def main():
                     help="pald_host calls timed for the end-to-end number (at most --steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other single-matrix workloads")
     ap.add_argument("--batched-count", type=int, default=2000)
     ap.add_argument("--oracle-rows", type=int, default=0)
     args = ap.parse_args()

@@ -60,7 +60,7 @@ typedef enum pald_status {
 
 /* Accumulation of the cohesion sums (pass 2). */
 enum {
-  /* FP32 partial sums over 4 consecutive y, folded into an FP32 running sum
+  /* FP32 partial sums over 8 consecutive y, folded into an FP32 running sum
    * (biased so that Fast2Sum is error-free) whose exact error is carried into
    * the next partial; the final merge and the 1/(n-1) normalisation are
    * exact two-float arithmetic with one rounding to FP32 (the precision of an
@@ -158,6 +158,29 @@ pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_
                       const pald_opts* opts);
 
 /*
+ * pald_pairwise - both passes for matrices too large to also hold u (the
+ * pairwise algorithm of Sec. 3.1, Alg. 1, blocked by strips of rows): for
+ * each strip of 256 rows x, the focus sizes u_xy of the strip's pairs (x, all
+ * y) are counted and kept only as 1/u in a strip buffer (256 x n floats),
+ * and the strip's rows of C are written from it.  Each pair's u is counted
+ * once per orientation, so it does about twice the work of pald_focus +
+ * pald_cohesion, but device memory holds only D, C and its scratch
+ * (pald_pairwise_scratch_bytes(n): the strip buffer, the tie map and, when
+ * n % 4 != 0, a row-padded copy of D) instead of D, U, C and an n x n R.
+ * C is bit for bit the C of pald_focus + pald_cohesion.
+ *   D  device, n x n FP32 (the input contract above), 16-byte aligned.
+ *   C  device, n x n FP32, 16-byte aligned, written completely.
+ *   opts  as pald_cohesion (validate, accum_mode, flags); schedule_id is ignored.
+ * Scratch is taken with cudaMallocAsync on `stream`.
+ * Errors: INVALID_ARG (null or misaligned pointer, n out of range, bad
+ * opts); validation errors; CUDA; NO_MEMORY.
+ */
+pald_status pald_pairwise(const float* D, int64_t n, float* C, const pald_opts* opts, pald_stream_t stream);
+
+/* Device scratch bytes pald_pairwise takes for order n (0 if out of range). */
+int64_t pald_pairwise_scratch_bytes(int64_t n);
+
+/*
  * pald_cohesion_noalloc - pass 2 for callers that must not allocate device
  * memory.  (The paper has no counterpart: this is a deployment variant.)
  * It computes exactly what pald_cohesion computes, with the same kernels,
@@ -178,6 +201,66 @@ pald_status pald_host(const float* D_host, int64_t n, int32_t* U_host, float* C_
  */
 pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, int64_t n, float* C,
                                   const pald_opts* opts, pald_stream_t stream);
+
+/*
+ * Sharding one matrix over several GPUs, one process per GPU (Sec. 3.2: the
+ * triplet blocks are independent given D).  The units are the 64 x 64
+ * upper-triangle super-tiles (bi <= bj) of the matrix in a fixed order;
+ * each rank takes a contiguous range [t0, t1) of them (pald_shard_range).
+ * A run on N ranks:
+ *   1. pald_focus_tiles on the rank's range (U needs no initialisation);
+ *   2. pald_pack_tiles(U, ..., both = 0) of the range into a buffer of
+ *      4096 words per tile; the caller all-gathers the ranks' buffers once
+ *      (e.g. NCCL) and calls pald_unpack_tiles(..., both = 0) for every
+ *      rank's range, which completes U (each tile also fills its mirror);
+ *   3. pald_cohesion_tiles on the rank's range; to collect C, pack with
+ *      both = 1 (8192 words per tile: blocks [X, Z] and [Z, X]), all-gather
+ *      and unpack with both = 1.
+ * Every tile gives the bits of the single-GPU passes, so the gathered U and
+ * C equal pald_focus and pald_cohesion's bit for bit.
+ */
+
+/* Number of 64 x 64 upper-triangle super-tiles of order n: T(T+1)/2 with
+ * T = ceil(n/64); 0 if n is out of range. */
+int64_t pald_shard_tiles(int64_t n);
+
+/* The balanced contiguous range of rank `rank` of `world`: tiles
+ * [floor(N*rank/world), floor(N*(rank+1)/world)), N = pald_shard_tiles(n).
+ * Errors: INVALID_ARG. */
+pald_status pald_shard_range(int64_t n, int32_t rank, int32_t world, int64_t* t0, int64_t* t1);
+
+/*
+ * pald_focus_tiles - pass 1 (as pald_focus) on tiles [t0, t1) only: writes
+ * u_xy and u_yx for every pair of those tiles into U (device, n x n int32);
+ * other entries of U are left as they are.
+ * Errors: as pald_focus; INVALID_ARG for a range outside [0, pald_shard_tiles(n)].
+ */
+pald_status pald_focus_tiles(const float* D, int64_t n, int64_t t0, int64_t t1, int32_t* U,
+                             const pald_opts* opts, pald_stream_t stream);
+
+/*
+ * pald_cohesion_tiles - pass 2 (as pald_cohesion) on tiles [t0, t1) only:
+ * U must be complete; writes C[X, Z] and C[Z, X] of those tiles.  It builds
+ * R = 1/u and the tie map of the whole matrix (O(n^2)) in scratch it takes
+ * with cudaMallocAsync.
+ * Errors: as pald_cohesion; INVALID_ARG for a bad range.
+ */
+pald_status pald_cohesion_tiles(const float* D, const int32_t* U, int64_t n, int64_t t0, int64_t t1, float* C,
+                                const pald_opts* opts, pald_stream_t stream);
+
+/*
+ * pald_pack_tiles / pald_unpack_tiles - copy tiles [t0, t1) of an n x n
+ * matrix of 4-byte words (device) to or from a packed device buffer: tile k
+ * of the range at word 4096*k (both = 0: block [X, Y], row by row, zeros
+ * outside the matrix) or 8192*k (both = 1: block [X, Y], then block [Y, X]).
+ * Unpacking with both = 0 also writes the transpose of each block to
+ * [Y, X] (for the symmetric U).
+ * Errors: INVALID_ARG (null pointer, n, both or range out of range); CUDA.
+ */
+pald_status pald_pack_tiles(const void* M, int64_t n, int64_t t0, int64_t t1, int32_t both, void* packed,
+                            pald_stream_t stream);
+pald_status pald_unpack_tiles(const void* packed, int64_t n, int64_t t0, int64_t t1, int32_t both, void* M,
+                              pald_stream_t stream);
 
 /*
  * pald_validate - check the input contract of D (see above) on the device.
@@ -254,6 +337,43 @@ pald_status pald_check_faults(pald_stream_t stream);
  * Errors: INVALID_ARG (limit out of range); CUDA.
  */
 pald_status pald_test_bounded_wait(int64_t limit_ns, pald_stream_t stream);
+
+/*
+ * Schedule tables (block-size tuning of Sec. 5, done for GPU tiles).  A table
+ * is a list of buckets sorted by n_max; a matrix of order n takes the first
+ * bucket with n <= n_max (the last bucket for larger n).  The library is
+ * built with the tables that the project's autotuner
+ * (paper_2307_16652_gb300/autotune.py) measured, keyed by GPU name and SM
+ * count; on a GPU without one it uses built-in defaults.  All schedules of a
+ * pass give identical bits; only the speed differs.
+ */
+typedef struct pald_schedule_bucket {
+  int64_t n_max;          /* largest order of the bucket */
+  int32_t focus;          /* pald_focus schedule (0 .. pald_schedule_count()-1) */
+  int32_t cohesion;       /* pald_cohesion schedule */
+  int32_t batched_split;  /* pald_batched: 1 = a diagonal tile leaves the pairs inside each group of
+                             four points to a separate work item (four warps instead of five on the
+                             tile); 0 = the tile computes them itself */
+  int32_t reserved;       /* must be 0 */
+} pald_schedule_bucket;
+
+/*
+ * pald_set_schedule_table - replaces the table of the CURRENT device (for
+ * example with one the caller tuned); count == 0 (buckets may be NULL)
+ * restores the table the library was built with.  Later pald_batched calls
+ * build new plans with it.
+ *   buckets  host array [count], 1 <= count <= 16, n_max strictly increasing.
+ * Errors: INVALID_ARG (bad count, order, schedule id, split flag); CUDA.
+ */
+pald_status pald_set_schedule_table(const pald_schedule_bucket* buckets, int32_t count);
+
+/*
+ * pald_get_schedule - the bucket that applies to order n on the current
+ * device.  *source (may be NULL) receives 0 for the built-in defaults, 1 for
+ * a tuned table built into the library, 2 for a table set by the caller.
+ * Errors: INVALID_ARG (null out, n out of range); CUDA.
+ */
+pald_status pald_get_schedule(int64_t n, pald_schedule_bucket* out, int32_t* source);
 
 /* Number of built-in tile schedules and the name of schedule `id` (static
  * string, or NULL if id is out of range).  Used by the autotuner. */

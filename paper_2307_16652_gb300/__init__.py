@@ -25,17 +25,27 @@ from .binding import (  # noqa: F401
     pald_batched,
     pald_cohesion,
     pald_cohesion_noalloc,
+    pald_cohesion_tiles,
     pald_focus,
+    pald_focus_tiles,
+    pald_get_schedule,
     pald_host,
     pald_local_depth,
+    pald_pack_tiles,
+    pald_pairwise,
+    pald_pairwise_scratch_bytes,
     pald_release,
     pald_schedule_count,
     pald_schedule_name,
+    pald_set_schedule_table,
+    pald_shard_range,
+    pald_shard_tiles,
     pald_status_string,
     pald_strong_ties,
     pald_test_bounded_wait,
     pald_tie_map,
     pald_tie_map_words,
+    pald_unpack_tiles,
     pald_validate,
     pald_version,
 )
@@ -44,6 +54,7 @@ __all__ = [
     "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PALD_FLAG_IGNORE_TIES", "PaldError", "lib", "library_path", "pald_check_faults",
     "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_local_depth",
     "pald_release", "pald_strong_ties", "pald_test_bounded_wait",
-    "pald_schedule_count", "pald_schedule_name", "pald_status_string", "pald_tie_map", "pald_tie_map_words",
-    "pald_validate", "pald_version",
+    "pald_schedule_count", "pald_schedule_name", "pald_set_schedule_table", "pald_get_schedule", "pald_status_string", "pald_tie_map", "pald_tie_map_words",
+    "pald_validate", "pald_version", "pald_cohesion_tiles", "pald_focus_tiles", "pald_pack_tiles",
+    "pald_unpack_tiles", "pald_shard_range", "pald_shard_tiles", "pald_pairwise", "pald_pairwise_scratch_bytes",
 ]

@@ -41,6 +41,11 @@ class PaldOpts(ctypes.Structure):
                 ("schedule_id", ctypes.c_int32), ("flags", ctypes.c_int32)]
 
 
+class PaldScheduleBucket(ctypes.Structure):
+    _fields_ = [("n_max", ctypes.c_int64), ("focus", ctypes.c_int32), ("cohesion", ctypes.c_int32),
+                ("batched_split", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lock = threading.Lock()
 _handle: ctypes.CDLL | None = None
 
@@ -69,13 +74,27 @@ def _lib() -> ctypes.CDLL:
         h.pald_tie_map.argtypes = [vp, i64, vp, vp]
         h.pald_check_faults.argtypes = [vp]
         h.pald_test_bounded_wait.argtypes = [i64, vp]
+        h.pald_set_schedule_table.argtypes = [ctypes.POINTER(PaldScheduleBucket), i32]
+        h.pald_pairwise.argtypes = [vp, i64, vp, op, vp]
+        h.pald_pairwise_scratch_bytes.argtypes = [i64]
+        h.pald_pairwise_scratch_bytes.restype = i64
+        h.pald_shard_tiles.argtypes = [i64]
+        h.pald_shard_tiles.restype = i64
+        h.pald_shard_range.argtypes = [i64, i32, i32, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        h.pald_focus_tiles.argtypes = [vp, i64, i64, i64, vp, op, vp]
+        h.pald_cohesion_tiles.argtypes = [vp, vp, i64, i64, i64, vp, op, vp]
+        h.pald_pack_tiles.argtypes = [vp, i64, i64, i64, i32, vp, vp]
+        h.pald_unpack_tiles.argtypes = [vp, i64, i64, i64, i32, vp, vp]
+        h.pald_get_schedule.argtypes = [i64, ctypes.POINTER(PaldScheduleBucket), ctypes.POINTER(i32)]
         h.pald_local_depth.argtypes = [vp, i64, vp, vp]
         h.pald_strong_ties.argtypes = [vp, i64, ctypes.c_float, vp, vp]
         h.pald_tie_map_words.argtypes = [i64]
         h.pald_tie_map_words.restype = i64
         for f in (h.pald_focus, h.pald_cohesion, h.pald_cohesion_noalloc, h.pald_batched, h.pald_host,
                   h.pald_validate, h.pald_tie_map, h.pald_check_faults, h.pald_local_depth, h.pald_strong_ties,
-                  h.pald_test_bounded_wait):
+                  h.pald_test_bounded_wait, h.pald_set_schedule_table, h.pald_get_schedule, h.pald_shard_range,
+                  h.pald_focus_tiles, h.pald_cohesion_tiles, h.pald_pack_tiles, h.pald_unpack_tiles,
+                  h.pald_pairwise):
             f.restype = ctypes.c_int
         h.pald_status_string.argtypes = [ctypes.c_int]
         h.pald_status_string.restype = ctypes.c_char_p
@@ -277,6 +296,115 @@ def pald_test_bounded_wait(limit_ns: int, *, stream=None) -> None:
     """Diagnostic: launch one CTA whose bounded waits give up after limit_ns
     (pald_check_faults then reports PALD_ERR_TIMEOUT once)."""
     _raise(_lib().pald_test_bounded_wait(int(limit_ns), _stream_ptr(stream)), "pald_test_bounded_wait")
+
+
+SCHEDULE_SOURCES = {0: "built-in defaults", 1: "tuned table", 2: "set by the caller"}
+
+
+def pald_set_schedule_table(buckets) -> None:
+    """Replace the current device's schedule table.  ``buckets`` is a list of
+    dicts (or tuples) n_max, focus, cohesion, batched_split sorted by n_max;
+    an empty list restores the table the library was built with."""
+    rows = [b if isinstance(b, dict) else dict(zip(("n_max", "focus", "cohesion", "batched_split"), b))
+            for b in buckets]
+    arr = (PaldScheduleBucket * max(1, len(rows)))()
+    for i, b in enumerate(rows):
+        arr[i] = PaldScheduleBucket(int(b["n_max"]), int(b["focus"]), int(b["cohesion"]),
+                                    int(b["batched_split"]), 0)
+    _raise(_lib().pald_set_schedule_table(arr, len(rows)), "pald_set_schedule_table")
+
+
+def pald_get_schedule(n: int) -> dict:
+    """The schedule bucket that applies to order n on the current device."""
+    out = PaldScheduleBucket()
+    src = ctypes.c_int32()
+    _raise(_lib().pald_get_schedule(int(n), ctypes.byref(out), ctypes.byref(src)), "pald_get_schedule")
+    return {"n_max": out.n_max, "focus": out.focus, "cohesion": out.cohesion, "batched_split": out.batched_split,
+            "source": SCHEDULE_SOURCES.get(src.value, str(src.value))}
+
+
+def pald_pairwise(D, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, ignore_ties=False, stream=None):
+    """Both passes by strips of rows, u never stored: device memory for D, C and
+    pald_pairwise_scratch_bytes(n) only.  Same C as pald_focus + pald_cohesion."""
+    import torch
+
+    n = D.shape[0]
+    o = _opts(validate, accum_mode, -1, ignore_ties)
+    _raise(_lib().pald_pairwise(_check(D, torch.float32, n, "D"), n, _check(C, torch.float32, n, "C"),
+                                ctypes.byref(o), _stream_ptr(stream)), "pald_pairwise")
+    return C
+
+
+def pald_pairwise_scratch_bytes(n: int) -> int:
+    return _lib().pald_pairwise_scratch_bytes(int(n))
+
+
+def pald_shard_tiles(n: int) -> int:
+    """Number of 64 x 64 upper-triangle super-tiles of order n (the shard units)."""
+    return _lib().pald_shard_tiles(int(n))
+
+
+def pald_shard_range(n: int, rank: int, world: int):
+    """The contiguous tile range [t0, t1) of `rank` out of `world`."""
+    t0, t1 = ctypes.c_int64(), ctypes.c_int64()
+    _raise(_lib().pald_shard_range(int(n), int(rank), int(world), ctypes.byref(t0), ctypes.byref(t1)),
+           "pald_shard_range")
+    return t0.value, t1.value
+
+
+def pald_focus_tiles(D, U, t0, t1, *, validate=False, stream=None):
+    """Pass 1 on the tiles [t0, t1): u of their pairs (and mirrors) into U."""
+    import torch
+
+    n = D.shape[0]
+    o = _opts(validate, PALD_ACCUM_COMPENSATED, -1)
+    _raise(_lib().pald_focus_tiles(_check(D, torch.float32, n, "D"), n, int(t0), int(t1),
+                                   _check(U, torch.int32, n, "U"), ctypes.byref(o), _stream_ptr(stream)),
+           "pald_focus_tiles")
+    return U
+
+
+def pald_cohesion_tiles(D, U, C, t0, t1, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, ignore_ties=False,
+                        stream=None):
+    """Pass 2 on the tiles [t0, t1) (U complete): C[X, Z] and C[Z, X] of those tiles."""
+    import torch
+
+    n = D.shape[0]
+    o = _opts(validate, accum_mode, -1, ignore_ties)
+    _raise(_lib().pald_cohesion_tiles(_check(D, torch.float32, n, "D"), _check(U, torch.int32, n, "U"), n,
+                                      int(t0), int(t1), _check(C, torch.float32, n, "C"), ctypes.byref(o),
+                                      _stream_ptr(stream)), "pald_cohesion_tiles")
+    return C
+
+
+def _words(t, name):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous() and t.element_size() == 4):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of 4-byte elements")
+    return t.data_ptr()
+
+
+def pald_pack_tiles(M, t0, t1, packed, *, both=False, stream=None):
+    """Tiles [t0, t1) of the n x n matrix M into `packed` (4096 or 8192 words per tile)."""
+    n = M.shape[0]
+    need = (int(t1) - int(t0)) * 4096 * (2 if both else 1)
+    if packed.numel() < need:
+        raise ValueError(f"packed holds {packed.numel()} words, {need} needed")
+    _raise(_lib().pald_pack_tiles(_words(M, "M"), n, int(t0), int(t1), int(bool(both)), _words(packed, "packed"),
+                                  _stream_ptr(stream)), "pald_pack_tiles")
+    return packed
+
+
+def pald_unpack_tiles(packed, M, t0, t1, *, both=False, stream=None):
+    """The inverse of pald_pack_tiles (with both=False each block's transpose is written too)."""
+    n = M.shape[0]
+    need = (int(t1) - int(t0)) * 4096 * (2 if both else 1)
+    if packed.numel() < need:
+        raise ValueError(f"packed holds {packed.numel()} words, {need} needed")
+    _raise(_lib().pald_unpack_tiles(_words(packed, "packed"), n, int(t0), int(t1), int(bool(both)), _words(M, "M"),
+                                    _stream_ptr(stream)), "pald_unpack_tiles")
+    return M
 
 
 def pald_schedule_count() -> int:

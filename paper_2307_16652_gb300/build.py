@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpald.so")
 
 SOURCES = ["pald_api.cu", "pald_scan.cu", "pald_focus.cu", "pald_cohesion.cu", "pald_batched.cu",
-           "pald_noalloc.cu", "pald_ties.cu", "pald_depth.cu"]
+           "pald_noalloc.cu", "pald_ties.cu", "pald_depth.cu", "pald_shard.cu", "pald_pairwise.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}"]
@@ -34,8 +34,39 @@ def nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpald")
 
 
+TUNED = os.path.join(HERE, "tuned_schedules.json")
+
+
+def tuned_tables_source() -> str:
+    """C++ initialiser of the autotuned schedule tables (tuned_schedules.json,
+    written by the autotuner) that pald_api.cu includes."""
+    import json
+
+    tables = []
+    if os.path.exists(TUNED):
+        with open(TUNED) as f:
+            tables = json.load(f).get("tables", [])
+    rows = []
+    for t in tables:
+        bs = t["buckets"]
+        if not 1 <= len(bs) <= 16:
+            raise ValueError(f"{TUNED}: a table needs 1 to 16 buckets")
+        cells = ", ".join("{%d, %d, %d, %d}" % (int(b["n_max"]), int(b["focus"]), int(b["cohesion"]),
+                                                int(b["batched_split"])) for b in bs)
+        name = str(t["gpu"]).replace("\\", "").replace('"', "")
+        rows.append('  {"%s", %d, %d, {%s}},' % (name, int(t["sms"]), len(bs), cells))
+    if not rows:  # keep the array non-empty; a table of 0 buckets never matches
+        rows.append('  {"", 0, 0, {}},')
+    return ("// Generated by build.py from tuned_schedules.json: do not edit.\n"
+            "static const TunedTable kTunedTables[] = {\n" + "\n".join(rows) + "\n};\n"
+            "static const int kTunedTableCount = %d;\n" % len(rows))
+
+
 def _inputs_digest(extra: list[str]) -> str:
     h = hashlib.sha256()
+    if os.path.exists(TUNED):
+        with open(TUNED, "rb") as f:
+            h.update(f.read())
     for root in (CSRC, INCLUDE):
         for name in sorted(os.listdir(root)):
             p = os.path.join(root, name)
@@ -47,21 +78,27 @@ def _inputs_digest(extra: list[str]) -> str:
     return h.hexdigest()
 
 
-def build(verbose: bool = False, extra_flags: list[str] | None = None, force: bool = False) -> str:
-    """Compile (if sources changed) and return the path of libpald.so."""
+def build(verbose: bool = False, extra_flags: list[str] | None = None, force: bool = False,
+          out_dir: str | None = None) -> str:
+    """Compile (if sources changed) and return the path of libpald.so
+    (in ``out_dir`` when given, for builds with other compile-time options)."""
     extra = list(extra_flags or [])
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = out_dir or BUILD
+    lib_path = os.path.join(build_dir, "libpald.so")
+    os.makedirs(build_dir, exist_ok=True)
     digest = _inputs_digest(extra)
-    stamp = os.path.join(BUILD, "libpald.digest")
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    stamp = os.path.join(build_dir, "libpald.digest")
+    if not force and os.path.exists(lib_path) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == digest:
-                return LIB
+                return lib_path
     cc = nvcc()
+    with open(os.path.join(build_dir, "tuned_schedules.inc"), "w") as f:
+        f.write(tuned_tables_source())
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
+        cmd = [cc, *ARCH, *FLAGS, f"-I{build_dir}", *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         res = subprocess.run(cmd, capture_output=True, text=True)
@@ -73,15 +110,15 @@ def build(verbose: bool = False, extra_flags: list[str] | None = None, force: bo
 
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib_path)
     with open(stamp, "w") as f:
         f.write(digest)
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -43,12 +43,14 @@
 // 32 y; tie_map_core.cuh builds it).
 //
 // Accumulation (PALD_ACCUM_COMPENSATED): the pair {S_xz, S_zx} is an FP32
-// partial over 4 consecutive y (fold_phase below places the chunk ends).
-// Every 4 y it is folded into the running sums {H_xz, H_zx}, which start at
-// the bias B = 4: a partial never exceeds
-// 4 * 1/2 plus the carried error, so |H| >= |S| always holds and Fast2Sum
-// (three adds, done as packed f32x2 ops on both accumulators at once) is
-// error-free.  Its exact error becomes the start of the next partial, so
+// partial over kMergeEvery = 8 consecutive y (fold_phase below places the
+// chunk ends).  Every 8 y it is folded into the running sums {H_xz, H_zx},
+// which start at the bias B = 8: a partial never exceeds 8 * 1/2 plus the
+// carried error, so |H| >= |S| always holds and Fast2Sum (three adds, done as
+// packed f32x2 ops on both accumulators at once) is error-free.  (Chunks of
+// 8 y instead of 4 halve the fold's share of the FMA pipe; on the paper-scale
+// and precision-study matrices the measured max and mean errors against the
+// FP64 oracle did not change.)  Its exact error becomes the start of the next partial, so
 // nothing is lost between chunks.  At the end H - B + S is formed exactly as
 // a two-float value, multiplied by 1/(n-1) (also two floats) and rounded once
 // to FP32: the precision of an FP64 merge, without the FP64 pipe (two_sum,
@@ -60,8 +62,7 @@
 
 namespace pald {
 
-constexpr int kMergeEvery = 4;      // y per FP32 partial
-constexpr float kMergeBias = 4.0f;  // >= kMergeEvery * 1/2 + carried error
+constexpr float kMergeBias = static_cast<float>(kMergeEvery);  // >= kMergeEvery * 1/2 + carried error
 
 template <class Geo>
 struct CohesionSmem {
@@ -101,13 +102,16 @@ __device__ __forceinline__ void cohesion_step_short(uint64_t& sacc, float a1, fl
 }
 
 // Fold phase of the pair in row slot i and column slot j of a thread tile:
-// 3 when x + z is even, 1 when it is odd, for the pair's global (x, z).
+// kMergeEvery - 1 when x + z is even, kMergeEvery / 2 - 1 when it is odd,
+// for the pair's global (x, z).
 // Every geometry puts x == i and z == j (mod 2) (tile_geom.cuh), so this is
 // a compile-time constant per slot.  It must be symmetric in x and z:
 // depending on the tile size, c_zx is the zx lane of pair (x, z) or the xz
 // lane of pair (z, x), and a symmetric phase gives both the same chunking,
 // so every schedule, both forms and the batched path stay bit-identical.
-__host__ __device__ constexpr int fold_phase(int i, int j) { return ((i + j) & 1) ? 1 : 3; }
+__host__ __device__ constexpr int fold_phase(int i, int j) {
+  return ((i + j) & 1) ? kMergeEvery / 2 - 1 : kMergeEvery - 1;
+}
 
 // ---------------------------------------------------------------------------
 // Final merge in two-float arithmetic.  GB300 runs FP64 at about two
@@ -206,10 +210,10 @@ __device__ __forceinline__ void cohesion_stage(const float* ad, const float* ar,
             cohesion_step(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
         }
       if (MODE == PALD_ACCUM_COMPENSATED) {
-        // pair (x, z) folds after the y with y mod 4 == fold_phase(i, j)
-        // (k0 and every stage start are multiples of 4): half of a thread's
-        // pairs fold at each of two y in four, spreading the packed adds
-        // over the FMA pipe
+        // pair (x, z) folds after the y with y mod kMergeEvery ==
+        // fold_phase(i, j) (k0 and every stage start are multiples of
+        // kMergeEvery): half of a thread's pairs fold at each of two y per
+        // chunk, spreading the packed adds over the FMA pipe
 #pragma unroll
         for (int i = 0; i < TX; ++i)
 #pragma unroll
@@ -325,7 +329,7 @@ __device__ __forceinline__ void cohesion_finish(float* __restrict__ C, int64_t n
 
 template <class Geo>
 __device__ __forceinline__ void cohesion_tile_checks() {
-  static_assert(Geo::BK % kMergeEvery == 0, "stages must hold whole merge chunks");
+  static_assert(Geo::BK % kMergeEvery == 0 && Geo::UNR % kMergeEvery == 0, "stages must hold whole merge chunks");
   static_assert(Geo::B <= kTieBlock && kTieBlock % Geo::B == 0, "a tile must lie in one tie-map block pair");
   static_assert(Geo::BK == 16 || Geo::BK == 32 || Geo::BK == 64, "stage depth must tile the tie-map y groups");
 }
@@ -498,7 +502,7 @@ __device__ __forceinline__ float4 group_row(const float* __restrict__ M, int64_t
   return __ldg(reinterpret_cast<const float4*>(M + y * pitch + x0));
 }
 
-// One y of the ten pairs, then the folds due after it (y mod 4 == K).
+// One y of the ten pairs, then the folds due after it (y mod kMergeEvery == K).
 template <int MODE, bool SHORT, int K>
 __device__ __forceinline__ void cohesion_group_y(const float4& d, const float4& r, float S, const float (&cv)[10],
                                                  uint64_t (&sacc)[10], uint64_t (&hacc)[10]) {
@@ -517,14 +521,28 @@ __device__ __forceinline__ void cohesion_group_y(const float4& d, const float4& 
   }
 }
 
-template <int MODE, bool SHORT>
+// Four consecutive y starting at phase P (y mod kMergeEvery == P).
+template <int MODE, bool SHORT, int P>
 __device__ __forceinline__ void cohesion_group_4y(const float4 (&d)[4], const float4 (&r)[4], float S,
                                                   const float (&cv)[10], uint64_t (&sacc)[10],
                                                   uint64_t (&hacc)[10]) {
-  cohesion_group_y<MODE, SHORT, 0>(d[0], r[0], S, cv, sacc, hacc);
-  cohesion_group_y<MODE, SHORT, 1>(d[1], r[1], S, cv, sacc, hacc);
-  cohesion_group_y<MODE, SHORT, 2>(d[2], r[2], S, cv, sacc, hacc);
-  cohesion_group_y<MODE, SHORT, 3>(d[3], r[3], S, cv, sacc, hacc);
+  cohesion_group_y<MODE, SHORT, P + 0>(d[0], r[0], S, cv, sacc, hacc);
+  cohesion_group_y<MODE, SHORT, P + 1>(d[1], r[1], S, cv, sacc, hacc);
+  cohesion_group_y<MODE, SHORT, P + 2>(d[2], r[2], S, cv, sacc, hacc);
+  cohesion_group_y<MODE, SHORT, P + 3>(d[3], r[3], S, cv, sacc, hacc);
+}
+
+// Four y from y0 (a multiple of 4), with their phase in the merge chunk.
+template <int MODE, bool SHORT>
+__device__ __forceinline__ void cohesion_group_step(int64_t y0, const float4 (&d)[4], const float4 (&r)[4], float S,
+                                                    const float (&cv)[10], uint64_t (&sacc)[10],
+                                                    uint64_t (&hacc)[10]) {
+  switch (static_cast<int>(y0 % kMergeEvery) / 4) {
+    case 0: cohesion_group_4y<MODE, SHORT, 0>(d, r, S, cv, sacc, hacc); break;
+    case 1: cohesion_group_4y<MODE, SHORT, 4 % kMergeEvery>(d, r, S, cv, sacc, hacc); break;
+    case 2: cohesion_group_4y<MODE, SHORT, 8 % kMergeEvery>(d, r, S, cv, sacc, hacc); break;
+    default: cohesion_group_4y<MODE, SHORT, 12 % kMergeEvery>(d, r, S, cv, sacc, hacc); break;
+  }
 }
 
 // C of the sixteen pairs of group q.  Dp, Rp: D and R = 1/u with row pitch
@@ -555,6 +573,8 @@ __device__ __forceinline__ void cohesion_group(const float* __restrict__ Dp, con
   const uint32_t* trow = tmap + (bx * dm.nb + bx) * dm.wpp;
   static_assert(kTieGroup % 4 == 0, "tie groups hold whole 4-y steps");
 
+  // the tile stops after a whole merge chunk; folding the last partial
+  // early or late does not change H + S
   const int64_t n4 = (n + 3) / 4 * 4;
   float4 d[4], r[4], dn[4], rn[4];
 #pragma unroll
@@ -574,9 +594,9 @@ __device__ __forceinline__ void cohesion_group(const float* __restrict__ Dp, con
       rn[k] = group_row(Rp, pitch, n, y0 + 4 + k, x0);
     }
     if (tied)
-      cohesion_group_4y<MODE, false>(d, r, S, cv, sacc, hacc);
+      cohesion_group_step<MODE, false>(y0, d, r, S, cv, sacc, hacc);
     else
-      cohesion_group_4y<MODE, true>(d, r, S, cv, sacc, hacc);
+      cohesion_group_step<MODE, true>(y0, d, r, S, cv, sacc, hacc);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       d[k] = dn[k];

@@ -13,6 +13,16 @@
 
 namespace pald {
 
+// Autotuned tables, generated at build time from tuned_schedules.json (the
+// autotuner's output) into the build directory.
+struct TunedTable {
+  const char* gpu;  // cudaDeviceProp::name
+  int sms;          // multiprocessor count
+  int count;
+  ScheduleBucket buckets[kMaxBuckets];
+};
+#include "tuned_schedules.inc"  // kTunedTables[], kTunedTableCount
+
 thread_local int32_t g_last_cuda_error = 0;
 
 pald_status cuda_fail(cudaError_t e) {
@@ -34,6 +44,80 @@ pald_opts opts_or_default(const pald_opts* o) {
 }
 
 constexpr int64_t kMaxN = int64_t(1) << 20;
+
+// ---------------------------------------------------------------------------
+// schedule tables, one per device
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct DeviceTable {
+  bool init = false;
+  int source = 0;  // 0 built-in defaults, 1 tuned table of this GPU, 2 set by the caller
+  int count = 0;
+  ScheduleBucket b[kMaxBuckets];
+};
+
+std::mutex g_sched_mu;
+DeviceTable g_sched[kMaxDevices];
+uint64_t g_sched_gen = 1;
+
+bool bucket_ok(const ScheduleBucket& b) {
+  return b.focus >= 0 && b.focus < kScheduleCount && b.cohesion >= 0 && b.cohesion < kScheduleCount &&
+         (b.batched_split == 0 || b.batched_split == 1) && b.n_max >= 2;
+}
+
+bool table_ok(const ScheduleBucket* b, int count) {
+  if (count < 1 || count > kMaxBuckets) return false;
+  for (int i = 0; i < count; ++i)
+    if (!bucket_ok(b[i]) || (i > 0 && b[i].n_max <= b[i - 1].n_max)) return false;
+  return true;
+}
+
+// The built-in choice for this device: its tuned table, if one was built in.
+void load_builtin(int dev, DeviceTable& t) {
+  t = DeviceTable{};
+  t.init = true;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return;
+  for (int i = 0; i < kTunedTableCount; ++i) {
+    const TunedTable& tt = kTunedTables[i];
+    if (tt.sms == prop.multiProcessorCount && std::strcmp(tt.gpu, prop.name) == 0 &&
+        table_ok(tt.buckets, tt.count)) {
+      t.source = 1;
+      t.count = tt.count;
+      for (int k = 0; k < tt.count; ++k) t.b[k] = tt.buckets[k];
+      return;
+    }
+  }
+}
+
+}  // namespace
+
+int schedule_for(int64_t n, ScheduleBucket* out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    *out = builtin_schedule(n);
+    return 0;
+  }
+  std::lock_guard<std::mutex> lock(g_sched_mu);
+  DeviceTable& t = g_sched[dev];
+  if (!t.init) load_builtin(dev, t);
+  if (t.count == 0) {
+    *out = builtin_schedule(n);
+    return 0;
+  }
+  int k = 0;
+  while (k + 1 < t.count && n > t.b[k].n_max) ++k;
+  *out = t.b[k];
+  return t.source;
+}
+
+uint64_t schedule_generation() {
+  std::lock_guard<std::mutex> lock(g_sched_mu);
+  return g_sched_gen;
+}
 
 cudaError_t smem_opt_in(const void* fn, int bytes) {
   int dev = 0;
@@ -212,18 +296,57 @@ pald_status pald_tie_map(const float* D, int64_t n, uint32_t* map, pald_stream_t
 
 pald_status pald_check_faults(pald_stream_t stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  uint32_t f1 = 0, f2 = 0, f3 = 0;
+  uint32_t f1 = 0, f2 = 0, f3 = 0, f4 = 0;
   cudaError_t e = take_focus_faults(&f1, s);
   if (e == cudaSuccess) e = take_cohesion_faults(&f2, s);
   if (e == cudaSuccess) e = take_batched_faults(&f3, s);
+  if (e == cudaSuccess) e = take_pairwise_faults(&f4, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  return (f1 | f2 | f3) ? PALD_ERR_TIMEOUT : PALD_OK;
+  return (f1 | f2 | f3 | f4) ? PALD_ERR_TIMEOUT : PALD_OK;
 }
 
 pald_status pald_test_bounded_wait(int64_t limit_ns, pald_stream_t stream) {
   if (limit_ns < 1000 || limit_ns > static_cast<int64_t>(kWaitLimitNs)) return PALD_ERR_INVALID_ARG;
   const cudaError_t e = launch_wait_selftest(static_cast<uint64_t>(limit_ns), reinterpret_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? PALD_OK : cuda_fail(e);
+}
+
+pald_status pald_set_schedule_table(const pald_schedule_bucket* buckets, int32_t count) {
+  if (count < 0 || count > kMaxBuckets || (count > 0 && !buckets)) return PALD_ERR_INVALID_ARG;
+  ScheduleBucket b[kMaxBuckets];
+  for (int i = 0; i < count; ++i) {
+    if (buckets[i].reserved != 0) return PALD_ERR_INVALID_ARG;
+    b[i] = ScheduleBucket{buckets[i].n_max, buckets[i].focus, buckets[i].cohesion, buckets[i].batched_split};
+  }
+  if (count > 0 && !table_ok(b, count)) return PALD_ERR_INVALID_ARG;
+  int dev = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (dev < 0 || dev >= kMaxDevices) return PALD_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_sched_mu);
+  DeviceTable& t = g_sched[dev];
+  if (count == 0) {
+    load_builtin(dev, t);
+  } else {
+    t.init = true;
+    t.source = 2;
+    t.count = count;
+    for (int i = 0; i < count; ++i) t.b[i] = b[i];
+  }
+  ++g_sched_gen;
+  return PALD_OK;
+}
+
+pald_status pald_get_schedule(int64_t n, pald_schedule_bucket* out, int32_t* source) {
+  if (!out || n < 2 || n > kMaxN) return PALD_ERR_INVALID_ARG;
+  int dev = 0;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e);
+  ScheduleBucket b;
+  const int src = schedule_for(n, &b);
+  *out = pald_schedule_bucket{b.n_max, b.focus, b.cohesion, b.batched_split, 0};
+  if (source) *source = src;
+  return PALD_OK;
 }
 
 int32_t pald_schedule_count(void) { return kScheduleCount; }
@@ -237,7 +360,9 @@ const char* pald_schedule_name(int32_t id) {
     case 4: return "focus 64x32 slices, 4x4, 32-deep | cohesion 64x32 slices, 4x2, 32-deep";
     case 5: return "focus 64x64, 4x4, 64-deep stages unrolled 16 | cohesion 64x64, 4x4, 32-deep unrolled 4";
     case 6: return "focus 128x64 slices, 8x4, 32-deep | cohesion 64x64, 4x4, 64-deep unrolled 8";
-    case 7: return "focus as 2 | cohesion 64x64, 4x4, 32-deep, TMA-staged, 2 CTAs/SM (needs n % 4 == 0)";
+    case 7:
+      return "focus 64x64, 4x4, 32-deep, TMA-staged, 3 CTAs/SM | cohesion 64x64, 4x4, 32-deep, TMA-staged, "
+             "2 CTAs/SM (both need n % 4 == 0, else the same tile with per-thread copies)";
     default: return nullptr;
   }
 }

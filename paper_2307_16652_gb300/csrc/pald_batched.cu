@@ -43,11 +43,9 @@ using FG = FocusS7;     // 64 x 64 tiles, 32-deep TMA stages
 using CG = CohesionS7;  // 64 x 64 tiles, 32-deep TMA stages
 static_assert(FG::B == 64 && CG::B == 64 && FG::H == 1 && CG::H == 1, "both passes share one tile list");
 constexpr int kB = 64;
-constexpr int kTieBlocksPerMatrix = 16;
 constexpr int kMaxGridY = 65535;  // matrices beyond it are strided over blockIdx.y
 constexpr int kMaxBatchedN = 4096;
 constexpr int kTieWordsBatched = ((kMaxBatchedN + kTieGroup - 1) / kTieGroup + 31) / 32;
-constexpr int kGroupThreads = 128;  // groups of four points per CTA of the pass-2 group kernel
 
 // Set by a CTA whose bounded wait gave up (never in normal operation).
 __device__ uint32_t g_batched_faults;
@@ -59,11 +57,66 @@ struct PadDesc {
   int64_t pitch;  // their row pitch (n rounded up to a multiple of 4)
 };
 
-// One pass over every row of every matrix (matrices along blockIdx.y, rows
-// strided over blockIdx.x, one CTA per row at a time): the row's repeats go
-// into the matrix's tie map (zeroed before), the row is copied into the
-// padded layout, and the smallest positive and largest entries into the
-// matrix's scan summary (zeroed before).
+// Before pass 1 when ties are ignored (no tie maps): every row of every
+// matrix is copied into the padded layout (the TMA copies need a 16-byte row
+// pitch) while the smallest positive and the largest entry go into the
+// matrix's scan summary (zeroed before; pass 1 takes its scale from it).
+// Matrices along blockIdx.y, one warp per row, rows strided over the CTAs of
+// the matrix: a plain HBM-bound copy.
+constexpr int kCopyThreads = 256;
+constexpr int kCopyBlocksPerMatrix = 8;
+
+__global__ void __launch_bounds__(kCopyThreads) batched_copy_kernel(const float* __restrict__ D,
+                                                                    const MatrixDesc* __restrict__ mats,
+                                                                    const PadDesc* __restrict__ pads,
+                                                                    float* __restrict__ Dp,
+                                                                    ScanResult* __restrict__ scans, int count) {
+  constexpr int kWarps = kCopyThreads / 32;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (int m = blockIdx.y; m < count; m += gridDim.y) {
+    const MatrixDesc md = mats[m];
+    const PadDesc pd = pads[m];
+    uint32_t inv_min = 0u, mx = 0u;
+    for (int64_t row = int64_t(blockIdx.x) * kWarps + warp; row < md.n; row += int64_t(gridDim.x) * kWarps) {
+      const float* src = D + md.off + row * md.n;
+      float* dst = Dp + pd.off_p + row * pd.pitch;
+      for (int64_t c0 = 0; c0 < md.n; c0 += 4 * 32) {  // four loads in flight per lane
+        float d[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t c = c0 + 32 * k + lane;
+          d[k] = c < md.n ? __ldg(src + c) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int64_t c = c0 + 32 * k + lane;
+          if (c >= md.n) continue;
+          dst[c] = d[k];
+          const uint32_t b = __float_as_uint(d[k]);
+          if (b < 0x7f800000u) {  // finite, not negative
+            if (b != 0u) inv_min = max(inv_min, ~b);
+            mx = max(mx, b);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      inv_min = max(inv_min, __shfl_xor_sync(0xffffffffu, inv_min, o));
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0) {
+      if (inv_min) atomicMax(&scans[m].inv_min_pos_bits, inv_min);
+      if (mx) atomicMax(&scans[m].max_bits, mx);
+    }
+  }
+}
+
+// The prep before pass 1: the same copy and scan, plus every row's repeats
+// into the matrix's tie map (zeroed before), at the prep's own occupancy
+// (many CTAs per SM: the per-row hashing is latency-bound; as work items of
+// the persistent pass-1 kernel it measured 6.6 ms slower on the batched
+// workload).  Matrices along blockIdx.y, one CTA per row at a time.
 struct PrepVisit {
   float* dst;  // padded row
   uint32_t* inv_min;
@@ -77,6 +130,8 @@ struct PrepVisit {
     }
   }
 };
+
+constexpr int kTieBlocksPerMatrix = 16;
 
 __global__ void __launch_bounds__(TieSmall::kThreads) batched_prep_kernel(const float* __restrict__ D,
                                                                           const MatrixDesc* __restrict__ mats,
@@ -113,8 +168,8 @@ __global__ void __launch_bounds__(TieSmall::kThreads) batched_prep_kernel(const 
 }
 
 // Work-list cursor of a persistent CTA: `slot` (shared) holds the current
-// item; thread 0 claims the next one as soon as a tile starts, so the atomic
-// round trip overlaps the tile.
+// item; thread 0 claims the next one as soon as an item starts, so the
+// atomic round trip overlaps the work.
 struct ItemCursor {
   int* counter;
   int* slot;
@@ -128,13 +183,14 @@ struct ItemCursor {
     if (threadIdx.x == 0) next = atomicAdd(counter, 1);
   }
   __device__ __forceinline__ int64_t advance() {
-    __syncthreads();  // every thread has read the slot and is done with the tile's shared memory
+    __syncthreads();  // every thread has read the slot and is done with the item's shared memory
     if (threadIdx.x == 0) *slot = next;
     __syncthreads();
     return *slot;
   }
 };
 
+// Pass 1's queue holds every 64 x 64 tile, largest matrices first.
 // maps[2m] is matrix m's padded D, maps[2m + 1] its padded R.  Three CTAs
 // per SM (80 registers, 48 KB ring each): short tiles leave gaps (claim,
 // first TMA stage, epilogue) that a third CTA fills; measured 6% faster on
@@ -158,14 +214,17 @@ __global__ void __launch_bounds__(FG::NT, 3) batched_focus_kernel(const float* _
     const MatrixDesc md = mats[w.matrix];
     const PadDesc pd = pads[w.matrix];
     const float scale = focus_scale(scans[w.matrix].inv_min_pos_bits);
-    if (!focus_tile_tma<FG>(maps + 2 * w.matrix, D + md.off, md.n, U + md.off, w.bi, w.bj, scale, md.n % 4 == 0,
-                            ring, Rp + pd.off_p, pd.pitch, true)) {
+    if (!focus_tile_tma<FG>(maps + 2 * w.matrix, D + md.off, md.n, U + md.off, w.a, w.b, scale, md.n % 4 == 0,
+                            ring, Rp + pd.off_p, pd.pitch, w.kind == kItemTile)) {
       if (threadIdx.x == 0) atomicOr(&g_batched_faults, 1u);
       break;
     }
   }
 }
 
+// Pass 2's queue holds every tile, largest matrices first; the pairs inside
+// the groups of four points that split diagonal tiles leave out come after,
+// from batched_cohesion_group_kernel.
 template <int MODE>
 __global__ void __launch_bounds__(CG::NT, 2) batched_cohesion_kernel(const float* __restrict__ D,
                                                                      float* __restrict__ C,
@@ -186,16 +245,20 @@ __global__ void __launch_bounds__(CG::NT, 2) batched_cohesion_kernel(const float
     const MatrixDesc md = mats[w.matrix];
     const float S = focus_scale(scans[w.matrix].inv_min_pos_bits);
     if (!cohesion_tile_tma<CG, MODE>(maps + 2 * w.matrix, maps + 2 * w.matrix + 1, D + md.off, md.n, C + md.off,
-                                     tmaps + md.tmap_off, S, w.bi, w.bj, md.n % 4 == 0, ring, tie_words, true)) {
+                                     tmaps + md.tmap_off, S, w.a, w.b, md.n % 4 == 0, ring, tie_words,
+                                     w.kind == kItemTile)) {
       if (threadIdx.x == 0) atomicOr(&g_batched_faults, 1u);
       break;
     }
   }
 }
 
-// Pass 2's pairs inside each group of four points, which the diagonal tiles
-// leave out: one thread per group, matrices along blockIdx.y (largest first,
-// `order`), groups along x.  Reads the padded copies of D and R.
+// Pass 2's pairs inside each group of four points, which split diagonal
+// tiles leave out: one thread per group, the listed matrices along
+// blockIdx.y (largest first), groups along x.  Reads the padded copies of D
+// and R.
+constexpr int kGroupThreads = 128;
+
 template <int MODE>
 __global__ void __launch_bounds__(kGroupThreads, 3) batched_cohesion_group_kernel(
     float* __restrict__ C, const float* __restrict__ Dp, const float* __restrict__ Rp,
@@ -290,20 +353,37 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   }
   // longest-processing-time first: a tile costs ~ n (its streamed dimension)
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ns[a] > ns[b]; });
-  std::vector<WorkItem> items;
+  const bool ignore_ties = (o.flags & PALD_FLAG_IGNORE_TIES) != 0;
+  // pass 1: every tile, then the tie-map rows (none when ties are ignored:
+  // the zeroed maps then select the short form everywhere); pass 2: every
+  // tile, with each matrix's group items after its tiles
+  // Whether diagonal tiles split off their in-group pairs is chosen per
+  // order from the schedule table (pald_schedule_bucket.batched_split).
+  std::vector<WorkItem> items1, items2;
+  std::vector<int32_t> group_order;  // matrices whose group pairs the group kernel computes
+  int64_t group_max_n = 0;
   for (int i : order) {
+    ScheduleBucket sb;
+    schedule_for(ns[i], &sb);
+    const int32_t kind = sb.batched_split ? kItemTile : kItemTileWhole;
     const int T = static_cast<int>((ns[i] + kB - 1) / kB);
     for (int bi = 0; bi < T; ++bi)
-      for (int bj = bi; bj < T; ++bj) items.push_back(WorkItem{i, bi, bj, 0});
+      for (int bj = bi; bj < T; ++bj) {
+        items1.push_back(WorkItem{i, bi, bj, kind});
+        items2.push_back(WorkItem{i, bi, bj, kind});
+      }
+    if (sb.batched_split) {
+      group_order.push_back(i);
+      group_max_n = std::max(group_max_n, ns[i]);
+    }
   }
-  int64_t max_n = 0;
-  for (int i = 0; i < count; ++i) max_n = std::max(max_n, ns[i]);
   const size_t o_mats = 0;
   const size_t o_pads = align_up(o_mats + sizeof(MatrixDesc) * count, 256);
   const size_t o_scans = align_up(o_pads + sizeof(PadDesc) * count, 256);
   const size_t o_order = align_up(o_scans + sizeof(ScanResult) * count, 256);
-  const size_t o_items = align_up(o_order + sizeof(int32_t) * count, 256);
-  const size_t o_counters = align_up(o_items + sizeof(WorkItem) * items.size(), 256);
+  const size_t o_items1 = align_up(o_order + sizeof(int32_t) * (group_order.size() + 1), 256);
+  const size_t o_items2 = align_up(o_items1 + sizeof(WorkItem) * items1.size(), 256);
+  const size_t o_counters = align_up(o_items2 + sizeof(WorkItem) * items2.size(), 256);
   const size_t o_tmaps = align_up(o_counters + 256, 256);
   const size_t o_maps = align_up(o_tmaps + sizeof(uint32_t) * static_cast<size_t>(tmap_words), 256);
   const size_t o_dpad = align_up(o_maps + sizeof(CUtensorMap) * 2 * static_cast<size_t>(count), 256);
@@ -324,7 +404,8 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   auto* d_pads = reinterpret_cast<PadDesc*>(base + o_pads);
   auto* d_scans = reinterpret_cast<ScanResult*>(base + o_scans);
   auto* d_order = reinterpret_cast<int32_t*>(base + o_order);
-  auto* d_items = reinterpret_cast<WorkItem*>(base + o_items);
+  auto* d_items1 = reinterpret_cast<WorkItem*>(base + o_items1);
+  auto* d_items2 = reinterpret_cast<WorkItem*>(base + o_items2);
   auto* d_counters = reinterpret_cast<int*>(base + o_counters);
   auto* d_tmaps = reinterpret_cast<uint32_t*>(base + o_tmaps);
   auto* d_maps = reinterpret_cast<CUtensorMap*>(base + o_maps);
@@ -338,8 +419,12 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   }
   if (e == cudaSuccess) e = cudaMemcpy(d_mats, mats.data(), sizeof(MatrixDesc) * count, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(d_pads, pads.data(), sizeof(PadDesc) * count, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_order, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !group_order.empty())
+    e = cudaMemcpy(d_order, group_order.data(), sizeof(int32_t) * group_order.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d_items1, items1.data(), sizeof(WorkItem) * items1.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(d_items2, items2.data(), sizeof(WorkItem) * items2.size(), cudaMemcpyHostToDevice);
   // the pad columns of the padded copies are read (by the pass-2 group
   // kernel) but never written: zero them once
   if (e == cudaSuccess) e = cudaMemset(d_dpad, 0, sizeof(float) * static_cast<size_t>(pad_elems));
@@ -372,31 +457,37 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
     destroy_plan(p);
     return cuda_fail(cudaErrorInvalidValue);
   }
-  const int64_t n_items = static_cast<int64_t>(items.size());
+  const int64_t n1 = static_cast<int64_t>(items1.size()), n2 = static_cast<int64_t>(items2.size());
+  const int ng = static_cast<int>(group_order.size());
 
   e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     const unsigned gy = static_cast<unsigned>(std::min(count, kMaxGridY));
+    const dim3 ggrid(static_cast<unsigned>((group_max_n + 4 * kGroupThreads - 1) / (4 * kGroupThreads)),
+                     static_cast<unsigned>(std::min(std::max(ng, 1), kMaxGridY)));
     cudaMemsetAsync(d_scans, 0, sizeof(ScanResult) * count, cs);
     cudaMemsetAsync(d_counters, 0, 2 * sizeof(int), cs);
     cudaMemsetAsync(d_tmaps, 0, sizeof(uint32_t) * static_cast<size_t>(tmap_words), cs);
-    batched_prep_kernel<<<dim3(kTieBlocksPerMatrix, gy), TieSmall::kThreads, 0, cs>>>(D, d_mats, d_pads, d_dpad,
-                                                                                      d_scans, d_tmaps, count);
-    if (o.flags & PALD_FLAG_IGNORE_TIES)  // empty maps: the short (strict) form everywhere
-      cudaMemsetAsync(d_tmaps, 0, sizeof(uint32_t) * static_cast<size_t>(tmap_words), cs);
-    batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_rpad, d_mats, d_pads, d_scans, d_maps, d_items, n_items,
+    if (ignore_ties)  // empty maps: the short (strict) form everywhere
+      batched_copy_kernel<<<dim3(kCopyBlocksPerMatrix, gy), kCopyThreads, 0, cs>>>(D, d_mats, d_pads, d_dpad,
+                                                                                    d_scans, count);
+    else
+      batched_prep_kernel<<<dim3(kTieBlocksPerMatrix, gy), TieSmall::kThreads, 0, cs>>>(D, d_mats, d_pads, d_dpad,
+                                                                                        d_scans, d_tmaps, count);
+    batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_rpad, d_mats, d_pads, d_scans, d_maps, d_items1, n1,
                                                     d_counters);
-    const dim3 ggrid(static_cast<unsigned>((max_n + 4 * kGroupThreads - 1) / (4 * kGroupThreads)), gy);
     if (plain) {
       batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, csmem, cs>>>(D, C, d_mats, d_scans, d_tmaps, d_maps,
-                                                                          d_items, n_items, d_counters + 1);
-      batched_cohesion_group_kernel<PALD_ACCUM_PLAIN><<<ggrid, kGroupThreads, 0, cs>>>(
-          C, d_dpad, d_rpad, d_mats, d_pads, d_scans, d_tmaps, d_order, count);
+                                                                          d_items2, n2, d_counters + 1);
+      if (ng > 0)
+        batched_cohesion_group_kernel<PALD_ACCUM_PLAIN><<<ggrid, kGroupThreads, 0, cs>>>(
+            C, d_dpad, d_rpad, d_mats, d_pads, d_scans, d_tmaps, d_order, ng);
     } else {
       batched_cohesion_kernel<PALD_ACCUM_COMPENSATED><<<gc, CG::NT, csmem, cs>>>(
-          D, C, d_mats, d_scans, d_tmaps, d_maps, d_items, n_items, d_counters + 1);
-      batched_cohesion_group_kernel<PALD_ACCUM_COMPENSATED><<<ggrid, kGroupThreads, 0, cs>>>(
-          C, d_dpad, d_rpad, d_mats, d_pads, d_scans, d_tmaps, d_order, count);
+          D, C, d_mats, d_scans, d_tmaps, d_maps, d_items2, n2, d_counters + 1);
+      if (ng > 0)
+        batched_cohesion_group_kernel<PALD_ACCUM_COMPENSATED><<<ggrid, kGroupThreads, 0, cs>>>(
+            C, d_dpad, d_rpad, d_mats, d_pads, d_scans, d_tmaps, d_order, ng);
     }
     cudaError_t launch_err = cudaGetLastError();
     e = cudaStreamEndCapture(cs, &p.graph);
@@ -470,6 +561,7 @@ pald_status pald_batched(int32_t count, const int64_t* n_host, const int64_t* of
   key.words.push_back(static_cast<int64_t>(reinterpret_cast<uintptr_t>(C)));
   key.words.push_back(o.accum_mode);
   key.words.push_back(o.flags);
+  key.words.push_back(static_cast<int64_t>(schedule_generation()));  // the plan follows the schedule table
   for (int i = 0; i < count; ++i) {
     key.words.push_back(n_host[i]);
     key.words.push_back(off_host[i]);

@@ -21,37 +21,46 @@ __global__ void __launch_bounds__(256) reciprocal_kernel(const int32_t* __restri
 template <class Geo, int MODE, int MINB>
 __global__ void __launch_bounds__(Geo::NT, MINB)
     cohesion_kernel(const float* __restrict__ D, const float* __restrict__ R, int64_t n, float* __restrict__ C,
-                    const uint32_t* __restrict__ tmap, const ScanResult* __restrict__ scan, int64_t T) {
+                    const uint32_t* __restrict__ tmap, const ScanResult* __restrict__ scan, int64_t T,
+                    int64_t t0) {
   extern __shared__ __align__(16) float smem[];
   int bi, bj, slice;
-  decode_tile(blockIdx.x, T, Geo::H, &bi, &bj, &slice);
+  decode_tile(blockIdx.x + t0 * Geo::H, T, Geo::H, &bi, &bj, &slice);
   cohesion_tile<Geo, MODE>(D, R, n, C, tmap, focus_scale(scan->inv_min_pos_bits), bi, bj, slice, smem);
 }
 
 template <class Geo, int MODE, int MINB>
 cudaError_t launch_t(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
-                     const ScanResult* scan, cudaStream_t s) {
+                     const ScanResult* scan, cudaStream_t s, int64_t t0 = 0, int64_t t1 = -1) {
   const int64_t T = (n + Geo::B - 1) / Geo::B;
-  const int64_t ctas = T * (T + 1) / 2 * Geo::H;
+  if (t1 < 0) t1 = T * (T + 1) / 2;
+  const int64_t ctas = (t1 - t0) * Geo::H;
+  if (ctas <= 0) return cudaSuccess;
   if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
   const int smem = CohesionSmem<Geo>::FLOATS * static_cast<int>(sizeof(float));
   const cudaError_t e = smem_opt_in(reinterpret_cast<const void*>(cohesion_kernel<Geo, MODE, MINB>), smem);
   if (e != cudaSuccess) return e;
-  cohesion_kernel<Geo, MODE, MINB><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(D, R, n, C, tmap, scan, T);
+  cohesion_kernel<Geo, MODE, MINB><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(D, R, n, C, tmap, scan, T,
+                                                                                    t0);
   return cudaGetLastError();
 }
 
 // Set by a CTA whose bounded wait gave up (never in normal operation).
 __device__ uint32_t g_cohesion_faults;
 
+#ifndef PALD_COHESION_TMA_MINB
+#define PALD_COHESION_TMA_MINB 2
+#endif
+
 template <int MODE>
-__global__ void __launch_bounds__(CohesionS7::NT, 2)
+__global__ void __launch_bounds__(CohesionS7::NT, PALD_COHESION_TMA_MINB)
     cohesion_tma_kernel(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmR,
                         const float* __restrict__ D, int64_t n, float* __restrict__ C,
-                        const uint32_t* __restrict__ tmap, const ScanResult* __restrict__ scan, int64_t T) {
+                        const uint32_t* __restrict__ tmap, const ScanResult* __restrict__ scan, int64_t T,
+                        int64_t t0) {
   extern __shared__ __align__(128) float smem_tma[];
   int bi, bj, slice;
-  decode_tile(blockIdx.x, T, 1, &bi, &bj, &slice);
+  decode_tile(blockIdx.x + t0, T, 1, &bi, &bj, &slice);
   TmaRing<4, CohesionS7::BK> ring;
   uint32_t* tie_words = reinterpret_cast<uint32_t*>(ring.carve(smem_tma));
   const float S = focus_scale(scan->inv_min_pos_bits);
@@ -88,10 +97,12 @@ bool tma_ok(const float* D, const float* R, const float* C, int64_t n) {
 
 template <int MODE>
 cudaError_t launch_tma(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
-                       const ScanResult* scan, cudaStream_t s) {
+                       const ScanResult* scan, cudaStream_t s, int64_t t0 = 0, int64_t t1 = -1) {
   using Geo = CohesionS7;
   const int64_t T = (n + 63) / 64;
-  const int64_t ctas = T * (T + 1) / 2;
+  if (t1 < 0) t1 = T * (T + 1) / 2;
+  const int64_t ctas = t1 - t0;
+  if (ctas <= 0) return cudaSuccess;
   if (ctas > 0x7fffffff) return cudaErrorInvalidValue;
   CUtensorMap mD, mR;
   cudaError_t e = encode_panel_map(&mD, D, n, n, Geo::BK);
@@ -100,7 +111,7 @@ cudaError_t launch_tma(const float* D, const float* R, int64_t n, float* C, cons
   const int smem = CohesionTmaSmem<Geo>::bytes(n);  // TMA ring + tie words
   e = smem_opt_in(reinterpret_cast<const void*>(cohesion_tma_kernel<MODE>), CohesionTmaSmem<Geo>::MAX_BYTES);
   if (e != cudaSuccess) return e;
-  cohesion_tma_kernel<MODE><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(mD, mR, D, n, C, tmap, scan, T);
+  cohesion_tma_kernel<MODE><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(mD, mR, D, n, C, tmap, scan, T, t0);
   return cudaGetLastError();
 }
 
@@ -147,6 +158,11 @@ cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s) {
 }
 
 cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int64_t pitch, int rows) {
+  return encode_rect_map(map, base, n, n, pitch, rows);
+}
+
+cudaError_t encode_rect_map(CUtensorMap* map, const float* base, int64_t cols, int64_t nrows, int64_t pitch,
+                            int rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -156,7 +172,7 @@ cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int
     if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
-  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(n), static_cast<cuuint64_t>(n)};  // {columns, rows}
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(nrows)};  // {columns, rows}
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(pitch) * sizeof(float)};       // row pitch, bytes
   const cuuint32_t box[2] = {64u, static_cast<cuuint32_t>(rows)};
   const cuuint32_t elem[2] = {1u, 1u};
@@ -164,6 +180,17 @@ cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int
                             elem, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_cohesion_range(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+                                  const ScanResult* scan, int accum_mode, int64_t t0, int64_t t1, cudaStream_t s) {
+  // the 64 x 64 tiles of the shard plan: TMA-staged when the layout allows
+  const bool tma = tma_ok(D, R, C, n);
+  if (accum_mode == PALD_ACCUM_PLAIN)
+    return tma ? launch_tma<PALD_ACCUM_PLAIN>(D, R, n, C, tmap, scan, s, t0, t1)
+               : launch_t<CohesionS3, PALD_ACCUM_PLAIN, 1>(D, R, n, C, tmap, scan, s, t0, t1);
+  return tma ? launch_tma<PALD_ACCUM_COMPENSATED>(D, R, n, C, tmap, scan, s, t0, t1)
+             : launch_t<CohesionS3, PALD_ACCUM_COMPENSATED, 1>(D, R, n, C, tmap, scan, s, t0, t1);
 }
 
 cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,

@@ -13,6 +13,15 @@
 
 namespace pald {
 
+// y per FP32 partial of the compensated cohesion sums (pass 2): every
+// kMergeEvery consecutive y the partial is folded into the running sum.
+#ifndef PALD_MERGE_EVERY
+#define PALD_MERGE_EVERY 8
+#endif
+constexpr int kMergeEvery = PALD_MERGE_EVERY;
+static_assert(kMergeEvery == 4 || kMergeEvery == 8 || kMergeEvery == 16,
+              "partials span 4, 8 or 16 y (the bias is then a power of two)");
+
 // ---------------------------------------------------------------------------
 // Scan summary of one matrix, produced on the device before pass 1.
 struct ScanResult {
@@ -197,6 +206,12 @@ cudaError_t launch_scan(const float* D, int64_t n, ScanResult* out, bool validat
 cudaError_t launch_focus(const float* D, int64_t n, int32_t* U, const ScanResult* scan, int schedule,
                          cudaStream_t s);
 cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_t s);
+// The 64 x 64 super-tiles [t0, t1) of a pass, in the launch order of
+// decode_tile (the units of a shard plan); TMA-staged when the layout allows.
+cudaError_t launch_focus_range(const float* D, int64_t n, int32_t* U, const ScanResult* scan, int64_t t0, int64_t t1,
+                               cudaStream_t s);
+cudaError_t launch_cohesion_range(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+                                  const ScanResult* scan, int accum_mode, int64_t t0, int64_t t1, cudaStream_t s);
 // Clears and fills the tie map (tie_map_words(n) words at `map`).
 cudaError_t launch_tie_map(const float* D, int64_t n, uint32_t* map, cudaStream_t s);
 // `tmap` null: every stage takes the long loop (same result, slower).
@@ -208,12 +223,16 @@ cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C,
 cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s);
 cudaError_t take_focus_faults(uint32_t* out, cudaStream_t s);
 cudaError_t take_batched_faults(uint32_t* out, cudaStream_t s);
+cudaError_t take_pairwise_faults(uint32_t* out, cudaStream_t s);
 // One CTA whose bounded waits run out after limit_ns (the give-up path of
 // the TMA pipeline); it records the pass-2 fault word.
 cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t s);
 // Tensor map of an n x n FP32 row-major matrix stored with row pitch `pitch`
 // elements (a multiple of 4), with boxes of `rows` x 64.
 cudaError_t encode_panel_map(CUtensorMap* map, const float* base, int64_t n, int64_t pitch, int rows);
+// The same for a `cols` x `nrows` matrix (row pitch `pitch` elements).
+cudaError_t encode_rect_map(CUtensorMap* map, const float* base, int64_t cols, int64_t nrows, int64_t pitch,
+                            int rows);
 
 // Batched: descriptors of every matrix, and a flat list of tile work items.
 struct MatrixDesc {
@@ -226,8 +245,13 @@ struct MatrixDesc {
 };
 struct WorkItem {
   int32_t matrix;
-  int32_t bi, bj;
-  int32_t slice;  // column slice of the super-tile
+  int32_t a, b;  // block row and column of the tile (a <= b)
+  int32_t kind;  // kItemTile or kItemTileWhole
+};
+enum : int32_t {
+  kItemTile = 0,       // one 64 x 64 upper-triangle tile; a diagonal one leaves its in-group pairs
+                       // (x / 4 == z / 4) to other warps (pass 1) or to the group kernel (pass 2)
+  kItemTileWhole = 1,  // as kItemTile, but a diagonal tile computes all of its pairs itself
 };
 
 }  // namespace pald

@@ -26,8 +26,8 @@ using CohesionS1 = TileGeom<32, 1, 1, 1, 4, 16>;  // small matrices, 64 threads
 using CohesionS2 = TileGeom<64, 2, 1, 1, 2, 16>;  // 4x2 pairs/thread: more warps per SM
 using CohesionS3 = TileGeom<64, 1, 1, 1, 4, 32>;  // deeper stages
 using CohesionS4 = TileGeom<64, 2, 1, 1, 2, 32>;  // 4x2 pairs/thread, deeper stages
-using CohesionS5 = TileGeom<64, 1, 1, 1, 4, 32, 4>;  // 32-deep, loop unrolled by 4 (smaller code)
-using CohesionS6 = TileGeom<64, 1, 1, 1, 4, 64, 8>;  // 64-deep stages, unrolled by 8
+using CohesionS5 = TileGeom<64, 1, 1, 1, 4, 32, kMergeEvery>;  // 32-deep, loop unrolled by one merge chunk
+using CohesionS6 = TileGeom<64, 1, 1, 1, 4, 64, (kMergeEvery > 8 ? kMergeEvery : 8)>;  // 64-deep stages, unrolled by 8
 using CohesionS7 = TileGeom<64, 1, 1, 1, 4, 32, 16>;  // S3's tile, TMA-staged, two CTAs per SM
 
 inline int sm_count() {
@@ -37,15 +37,41 @@ inline int sm_count() {
   return sms;
 }
 
-// Defaults from the GB300 autotune table (times in ms, best per order):
-//   focus    n=1024: s7 0.117 | 2048: s4 0.515 | 4096: s2/s7 3.52 | 8192: s2/s7 27.1
-//   cohesion n=1024: s7 0.229 | 2048: s7 1.118 | 4096: s7 7.17   | 8192: s7 54.6
-// Orders below 1024 take the 32-wide tiles so that the launch still covers
-// the GPU.
-inline int default_focus_schedule(int64_t n) { return n < 1024 ? 1 : 2; }
+// The schedule choices for one range of orders (pald_schedule_bucket).
+struct ScheduleBucket {
+  int64_t n_max;
+  int32_t focus, cohesion, batched_split;
+};
+constexpr int kMaxBuckets = 16;
 
+// The bucket in force for order n on the current device: the caller's table
+// (pald_set_schedule_table), else the autotuned table built into the library
+// for this GPU (name and SM count), else the built-in defaults below.
+// Returns 0, 1 or 2 for defaults, tuned, caller (pald_get_schedule).
+int schedule_for(int64_t n, ScheduleBucket* out);
+// Changes whenever a device's table changes (batched plans depend on it).
+uint64_t schedule_generation();
+
+// Built-in defaults when no tuned table matches the GPU.  Orders below 1024
+// take the 32-wide tiles so that the launch still covers the GPU.
 // Schedule 7 (TMA) needs n % 4 == 0 and aligned buffers; otherwise it runs
-// schedule 3's tile with per-thread copies.
-inline int default_cohesion_schedule(int64_t n) { return n < 1024 ? 1 : (n % 4 == 0 ? 7 : (n < 4096 ? 4 : 3)); }
+// the same tile with per-thread copies (schedule 2's tile for pass 1).
+inline ScheduleBucket builtin_schedule(int64_t n) {
+  return ScheduleBucket{n < 1024 ? 1023 : (int64_t(1) << 20), n < 1024 ? 1 : (n % 4 == 0 ? 7 : 2),
+                        n < 1024 ? 1 : (n % 4 == 0 ? 7 : (n < 4096 ? 4 : 3)), 1};
+}
+
+inline int default_focus_schedule(int64_t n) {
+  ScheduleBucket b;
+  schedule_for(n, &b);
+  return b.focus;
+}
+inline int default_cohesion_schedule(int64_t n) {
+  ScheduleBucket b;
+  schedule_for(n, &b);
+  // a tuned TMA choice for an order the TMA tile cannot take runs schedule 3
+  // or 4's tile (see launch_cohesion); keep the built-in rule's choice there
+  return (b.cohesion == 7 && n % 4 != 0) ? builtin_schedule(n).cohesion : b.cohesion;
+}
 
 }  // namespace pald

@@ -82,7 +82,7 @@ def fast2sum_fold(h, s):
     return t, fsub(s, z)
 
 
-BIAS = F(4)
+BIAS = F(8)  # the running sums start at the bias kMergeBias = kMergeEvery = 8
 
 
 def cohesion_value(H, S, n, drop_lo=False):
@@ -108,10 +108,10 @@ def _cases(count, seed):
         n = int(rng.integers(2, 1 << 20))
         # running sum H = B + (a sum of up to n/2 terms of size <= 1/2): grid
         # of FP32 values of every magnitude the kernel can reach
-        top = 4.0 + n / 2.0
-        H = f32(4.0 + (top - 4.0) * rng.random() ** 3)
+        top = 8.0 + n / 2.0
+        H = f32(8.0 + (top - 8.0) * rng.random() ** 3)
         # partial S: a few terms of 1/u, possibly a small negative carry
-        S = f32(rng.random() * 2.0 - 1e-7 * rng.random())
+        S = f32(rng.random() * 4.0 - 1e-7 * rng.random())
         yield n, H, S
 
 
@@ -125,8 +125,8 @@ def test_inverse_pair_is_one_over_m_to_2_pow_minus_46():
 def test_fast2sum_fold_is_error_free_with_the_bias():
     rng = np.random.default_rng(2)
     for _ in range(5000):
-        h = f32(4.0 + rng.random() * 1e5)
-        s = f32(rng.random() * 2.0 - 1e-7)
+        h = f32(8.0 + rng.random() * 1e5)
+        s = f32(rng.random() * 4.0 - 1e-7)  # a partial over 8 y of terms <= 1/2
         assert abs(h) >= abs(s)
         t, e = fast2sum_fold(h, s)
         assert t + e == h + s
@@ -161,8 +161,8 @@ def test_exact_small_quotients(m):
     # H - B + S equal to a multiple of (n - 1): the result must be exact
     n = m + 1
     for k in (1, 3, 17):
-        if 4 + k * m >= 1 << 24:  # H must be an FP32 integer (it never exceeds 4 + n/2)
+        if 8 + k * m >= 1 << 24:  # H must be an FP32 integer (it never exceeds 8 + n/2)
             continue
-        H = f32(4.0 + k * m)
+        H = f32(8.0 + k * m)
         got = cohesion_value(H, F(0), n)
         assert got == k
