@@ -67,7 +67,17 @@ enum {
    * FP64 merge) (default). */
   PALD_ACCUM_COMPENSATED = 0,
   /* one FP32 running sum per entry (precision baseline), normalised the same way */
-  PALD_ACCUM_PLAIN = 1
+  PALD_ACCUM_PLAIN = 1,
+  /* exact fixed-point sums (deterministic whatever the order of the terms):
+   * each 1/u_xy becomes the integer round(2^40 / u_xy), the half credits are
+   * kept exact, the sum over y is an exact integer, and one FP64 scaling by
+   * 2^-41 / (n-1) and one rounding give c_xz.  Relative error at most
+   * max(u) / 2^41 (3e-8 at n = 65536).  Permuting the points permutes C bit
+   * for bit.  Slower than the compensated mode (one CTA per SM, two weight
+   * arrays of n x n floats as scratch); pald_batched runs it matrix by matrix
+   * through the single-matrix path; pald_pairwise and pald_cohesion_noalloc
+   * do not take it (INVALID_ARG). */
+  PALD_ACCUM_FIXED = 2
 };
 
 /* Bits of pald_opts.flags. */
@@ -81,7 +91,7 @@ enum {
 
 typedef struct pald_opts {
   int32_t validate;     /* nonzero: check the input contract before computing */
-  int32_t accum_mode;   /* PALD_ACCUM_COMPENSATED or PALD_ACCUM_PLAIN */
+  int32_t accum_mode;   /* PALD_ACCUM_COMPENSATED, PALD_ACCUM_PLAIN or PALD_ACCUM_FIXED */
   int32_t schedule_id;  /* -1 = automatic tile schedule; >= 0 forces one (pald_schedule_name) */
   int32_t flags;        /* 0 (exact, the default) or PALD_FLAG_IGNORE_TIES; other bits must be 0 */
 } pald_opts;          /* a NULL opts pointer means {0, PALD_ACCUM_COMPENSATED, -1, 0} */

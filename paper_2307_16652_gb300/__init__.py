@@ -16,6 +16,7 @@ from __future__ import annotations
 
 from .binding import (  # noqa: F401
     PALD_ACCUM_COMPENSATED,
+    PALD_ACCUM_FIXED,
     PALD_ACCUM_PLAIN,
     PALD_FLAG_IGNORE_TIES,
     PaldError,
@@ -51,7 +52,7 @@ from .binding import (  # noqa: F401
 )
 
 __all__ = [
-    "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_PLAIN", "PALD_FLAG_IGNORE_TIES", "PaldError", "lib", "library_path", "pald_check_faults",
+    "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_FIXED", "PALD_ACCUM_PLAIN", "PALD_FLAG_IGNORE_TIES", "PaldError", "lib", "library_path", "pald_check_faults",
     "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_local_depth",
     "pald_release", "pald_strong_ties", "pald_test_bounded_wait",
     "pald_schedule_count", "pald_schedule_name", "pald_set_schedule_table", "pald_get_schedule", "pald_status_string", "pald_tie_map", "pald_tie_map_words",

@@ -17,6 +17,7 @@ from . import build as _build
 
 PALD_ACCUM_COMPENSATED = 0
 PALD_ACCUM_PLAIN = 1
+PALD_ACCUM_FIXED = 2
 PALD_FLAG_IGNORE_TIES = 1
 
 _STATUS = {

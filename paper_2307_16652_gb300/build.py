@@ -21,7 +21,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpald.so")
 
 SOURCES = ["pald_api.cu", "pald_scan.cu", "pald_focus.cu", "pald_cohesion.cu", "pald_batched.cu",
-           "pald_noalloc.cu", "pald_ties.cu", "pald_depth.cu", "pald_shard.cu", "pald_pairwise.cu"]
+           "pald_noalloc.cu", "pald_ties.cu", "pald_depth.cu", "pald_shard.cu", "pald_pairwise.cu", "pald_fixed.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", f"-I{INCLUDE}"]

@@ -489,19 +489,6 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
 // partial into H leaves H + S, and so the merged value, unchanged: stopping
 // at the first multiple of 4 past n gives the same bits.
 
-__device__ __forceinline__ float comp4(const float4& v, int i) {
-  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
-}
-
-// Row y, columns x0 .. x0+3 of a matrix of order n with row pitch `pitch`
-// (a multiple of 4, 16-byte aligned rows; the columns up to the pitch
-// exist); zeros for y >= n.
-__device__ __forceinline__ float4 group_row(const float* __restrict__ M, int64_t pitch, int64_t n, int64_t y,
-                                            int64_t x0) {
-  if (y >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
-  return __ldg(reinterpret_cast<const float4*>(M + y * pitch + x0));
-}
-
 // One y of the ten pairs, then the folds due after it (y mod kMergeEvery == K).
 template <int MODE, bool SHORT, int K>
 __device__ __forceinline__ void cohesion_group_y(const float4& d, const float4& r, float S, const float (&cv)[10],

@@ -331,6 +331,19 @@ __device__ __forceinline__ void focus_tile(const float* __restrict__ D, int64_t 
 // a kernel of its own: beside pass 2's long unrolled loops the extra
 // shared-memory reads of in-tile group warps cost more than they save.)
 
+__device__ __forceinline__ float comp4(const float4& v, int i) {
+  return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w));
+}
+
+// Row y, columns x0 .. x0+3 of a matrix of order n with row pitch `pitch`
+// (a multiple of 4, 16-byte aligned rows; the columns up to the pitch
+// exist); zeros for y >= n.
+__device__ __forceinline__ float4 group_row(const float* __restrict__ M, int64_t pitch, int64_t n, int64_t y,
+                                            int64_t x0) {
+  if (y >= n) return make_float4(0.f, 0.f, 0.f, 0.f);
+  return __ldg(reinterpret_cast<const float4*>(M + y * pitch + x0));
+}
+
 // Pair k = 0..9 of a group: (i, j) with i <= j, row by row.
 __host__ __device__ constexpr int group_pair_i(int k) { return k < 4 ? 0 : (k < 7 ? 1 : (k < 9 ? 2 : 3)); }
 __host__ __device__ constexpr int group_pair_j(int k) {
@@ -455,6 +468,92 @@ __device__ __forceinline__ bool focus_tile_tma(const CUtensorMap* tmD, const flo
     focus_finish<Geo>(U, n, X0, int64_t(bj) * 64, tx, ty, tx != ty || bi != bj, vec, acc, R, rpitch);
   if (ok && grp) focus_group_finish(U, n, X0, GroupPairs(threadIdx.x, rows), {acc[0][0], acc[0][1]}, R, rpitch);
   return ok;
+}
+
+// ---------------------------------------------------------------------------
+// Two diagonal tiles in one CTA (batched pass 1).  A diagonal 64 x 64 tile
+// without its in-group pairs has 120 4 x 4 blocks strictly above its
+// diagonal: four warps' worth.  Alone it would leave half of a CTA's warps
+// idle for a whole tile; here threads 0..127 take the blocks of diagonal
+// tile (ba, ba) and threads 128..255 those of (bb, bb) of the same matrix
+// (bb < 0: the second half idles), each half reading its own panel of the
+// stage (D[z][Xa] and D[z][Xb]).  The pairs inside the groups of four
+// points are left to focus_group.  Counts are exact, so the bits are the
+// single tile's.  Returns false when a wait ran out of time.
+template <class Geo>
+__device__ __forceinline__ bool focus_diag_pair_tma(const CUtensorMap* tmD, const float* __restrict__ D, int64_t n,
+                                                    int32_t* __restrict__ U, int ba, int bb, float scale, bool vec,
+                                                    TmaRing<2, Geo::BK>& ring, float* __restrict__ R,
+                                                    int64_t rpitch) {
+  static_assert(Geo::BX == 64 && Geo::BY == 64 && Geo::NT == 256, "pairs of 64 x 64 tiles on 256 threads");
+  constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY;
+  const int half = static_cast<int>(threadIdx.x) / 128;  // warp-uniform
+  const int bi = half == 0 ? ba : bb;
+  int tx = 0, ty = 0;  // an idle half keeps a valid placement (its setup loads stay in the matrix)
+  const bool active = bi >= 0 && tile_block_64(bi, bi, n, threadIdx.x % 128, &tx, &ty, true);
+  const int64_t X0 = int64_t(bi >= 0 ? bi : ba) * 64;
+  const int nstages = static_cast<int>((n + BK - 1) / BK);
+  constexpr int CH = 16;
+  if (threadIdx.x == 0) ring.init();
+  __syncthreads();
+  float cst[TX][TY];
+  uint64_t acc[TX][TY];
+  focus_init<Geo>(D, n, X0, X0, tx, ty, scale, cst, acc);
+  const CUtensorMap* const maps[2] = {tmD, tmD};
+  const int cols[2] = {ba * 64, (bb >= 0 ? bb : ba) * 64};
+  const bool ok = tma_pipeline(ring, nstages, [&](int q) { ring.issue(q, maps, cols); },
+                               [&](int st, int buf) {
+                                 if (active)
+                                   focus_stage<Geo, CH>(ring.panel(buf, half), ring.panel(buf, half), tx, ty, scale,
+                                                        cst, acc, stage_extent<BK, CH>(n, st));
+                               });
+  __syncthreads();
+  if (threadIdx.x == 0) ring.inval();
+  // every block is strictly above the diagonal: its mirror is written too
+  if (ok && active) focus_finish<Geo>(U, n, X0, X0, tx, ty, true, vec, acc, R, rpitch);
+  return ok;
+}
+
+// The pairs inside group q of four points x0 .. x0+3 (x0 = 4q), both orders
+// and the diagonal, for pass 1: one thread streams z through the group's
+// four columns of row z (one 16-byte vector of the row-padded copy Dp:
+// d_zx = d_xz by symmetry) and counts [min(d_xz, d_x'z) > d_xx'] for the ten
+// pairs x <= x'.  Writes u to U (row pitch n) and 1/u (recip_entry) to R
+// (row pitch `rpitch`).  Exact counts: the bits of the tile code.  (Its cost
+// is one read of Dp from HBM: the matrix's data has left L2 by then.)
+__device__ __forceinline__ void focus_group(const float* __restrict__ Dp, int64_t pitch, int64_t n, int64_t q,
+                                            float scale, int32_t* __restrict__ U, float* __restrict__ R,
+                                            int64_t rpitch) {
+  const int64_t x0 = 4 * q;
+  float cst[10];
+  {
+    float4 row[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) row[i] = group_row(Dp, pitch, n, x0 + i, x0);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) cst[k] = -comp4(row[group_pair_i(k)], group_pair_j(k)) * scale;  // exact
+  }
+  float cnt[10];
+#pragma unroll
+  for (int k = 0; k < 10; ++k) cnt[k] = 0.f;
+#pragma unroll 4
+  for (int64_t z = 0; z < n; ++z) {
+    const float4 d = group_row(Dp, pitch, n, z, x0);
+#pragma unroll
+    for (int k = 0; k < 10; ++k)
+      cnt[k] += ffma_sat(fmin_(comp4(d, group_pair_i(k)), comp4(d, group_pair_j(k))), scale, cst[k]);
+  }
+  const int nn = static_cast<int>(n);
+#pragma unroll
+  for (int k = 0; k < 10; ++k) {
+    const int64_t x = x0 + group_pair_i(k), y = x0 + group_pair_j(k);
+    if (x >= n || y >= n) continue;
+    const int32_t u = nn - static_cast<int32_t>(cnt[k]);  // an exact count below 2^24
+    U[x * n + y] = u;
+    U[y * n + x] = u;
+    R[x * rpitch + y] = recip_entry(u, x, y);
+    R[y * rpitch + x] = recip_entry(u, y, x);
+  }
 }
 
 }  // namespace pald

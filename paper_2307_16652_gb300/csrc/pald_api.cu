@@ -33,7 +33,9 @@ pald_status cuda_fail(cudaError_t e) {
 bool opts_ok(const pald_opts* o) {
   if (!o) return true;
   if ((o->flags & ~PALD_FLAG_IGNORE_TIES) != 0) return false;
-  if (o->accum_mode != PALD_ACCUM_COMPENSATED && o->accum_mode != PALD_ACCUM_PLAIN) return false;
+  if (o->accum_mode != PALD_ACCUM_COMPENSATED && o->accum_mode != PALD_ACCUM_PLAIN &&
+      o->accum_mode != PALD_ACCUM_FIXED)
+    return false;
   if (o->schedule_id < -1 || o->schedule_id >= kScheduleCount) return false;
   return true;
 }
@@ -173,6 +175,27 @@ struct Scratch {
   }
 };
 
+// Pass 2 in fixed point (PALD_ACCUM_FIXED) on tiles [t0, t1) (t1 < 0: all):
+// scan, tie map, the integer weight pieces, then the exact tiles.
+pald_status cohesion_fixed(const float* D, const int32_t* U, int64_t n, float* C, const pald_opts& o, int64_t t0,
+                           int64_t t1, cudaStream_t s) {
+  const size_t fbytes = (fixed_scratch_bytes(D, n) + 255) / 256 * 256;
+  const size_t tbytes = (static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t) + 255) / 256 * 256;
+  Scratch scratch(s);
+  cudaError_t e = scratch.alloc(fbytes + tbytes + 256);
+  if (e != cudaSuccess) return cuda_fail(e);
+  auto* tmap = reinterpret_cast<uint32_t*>(static_cast<char*>(scratch.p) + fbytes);
+  auto* scan = reinterpret_cast<ScanResult*>(static_cast<char*>(scratch.p) + fbytes + tbytes);
+  const pald_status st = scan_and_check(D, n, scan, o.validate != 0, s);
+  if (st != PALD_OK) return st;
+  if (o.flags & PALD_FLAG_IGNORE_TIES)
+    e = cudaMemsetAsync(tmap, 0, static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t), s);
+  else
+    e = launch_tie_map(D, n, tmap, s);
+  if (e == cudaSuccess) e = launch_fixed_cohesion(D, U, n, C, tmap, scan, scratch.p, t0, t1, s);
+  return e == cudaSuccess ? PALD_OK : cuda_fail(e);
+}
+
 }  // namespace pald
 
 using namespace pald;
@@ -199,6 +222,7 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
   if (!D || !U || !C || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
   const pald_opts o = opts_or_default(opts);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (o.accum_mode == PALD_ACCUM_FIXED) return cohesion_fixed(D, U, n, C, o, 0, -1, s);
   // scratch: R = 1/u (n x n FP32), the tie map, the scan summary
   const size_t rbytes = static_cast<size_t>(n) * static_cast<size_t>(n) * sizeof(float);
   const size_t tbytes = (static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t) + 255) / 256 * 256;
@@ -296,13 +320,14 @@ pald_status pald_tie_map(const float* D, int64_t n, uint32_t* map, pald_stream_t
 
 pald_status pald_check_faults(pald_stream_t stream) {
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  uint32_t f1 = 0, f2 = 0, f3 = 0, f4 = 0;
+  uint32_t f1 = 0, f2 = 0, f3 = 0, f4 = 0, f5 = 0;
   cudaError_t e = take_focus_faults(&f1, s);
   if (e == cudaSuccess) e = take_cohesion_faults(&f2, s);
   if (e == cudaSuccess) e = take_batched_faults(&f3, s);
   if (e == cudaSuccess) e = take_pairwise_faults(&f4, s);
+  if (e == cudaSuccess) e = take_fixed_faults(&f5, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  return (f1 | f2 | f3 | f4) ? PALD_ERR_TIMEOUT : PALD_OK;
+  return (f1 | f2 | f3 | f4 | f5) ? PALD_ERR_TIMEOUT : PALD_OK;
 }
 
 pald_status pald_test_bounded_wait(int64_t limit_ns, pald_stream_t stream) {

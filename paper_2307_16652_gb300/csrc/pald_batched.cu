@@ -16,11 +16,15 @@
 // atomic counter (claiming the one after it while the tile runs) and runs
 // the TMA tile code of the single-matrix kernels on the item's matrix.  A
 // CTA that finds the list exhausted exits; the only waits are the bounded
-// mbarrier waits of the TMA ring.  Diagonal tiles run their 4 x 4 blocks
-// above the diagonal on four warps, so they cost about half a full tile; the
-// pairs inside the groups of four points go, in pass 1, to the tile's other
-// four warps (GroupPairs in focus_core.cuh) and, in pass 2, to a kernel with
-// one thread per group after the tiles (cohesion_group in cohesion_core.cuh).
+// mbarrier waits of the TMA ring.  A diagonal tile without the pairs inside
+// its groups of four points has four warps' worth of 4 x 4 blocks, so the
+// diagonal tiles of a matrix come in pairs: pass 1 runs the two on the two
+// halves of one CTA (focus_diag_pair_tma), pass 2 one after the other.  The
+// in-group pairs go to a kernel with one thread per group after each pass
+// (focus_group, cohesion_group).  Measured choices: tie maps as work items at
+// pass 1's tail were 6.6 ms slower than in the prep kernel, parallel graph
+// branches for the side kernels no faster than one chain, a pass-2 pair on
+// two CTA halves no faster than in sequence.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -46,6 +50,7 @@ constexpr int kB = 64;
 constexpr int kMaxGridY = 65535;  // matrices beyond it are strided over blockIdx.y
 constexpr int kMaxBatchedN = 4096;
 constexpr int kTieWordsBatched = ((kMaxBatchedN + kTieGroup - 1) / kTieGroup + 31) / 32;
+constexpr int kGroupThreads = 128;  // groups of four points per CTA of the group kernels
 
 // Set by a CTA whose bounded wait gave up (never in normal operation).
 __device__ uint32_t g_batched_faults;
@@ -132,14 +137,20 @@ struct PrepVisit {
 };
 
 constexpr int kTieBlocksPerMatrix = 16;
+#ifndef PALD_PREP_THREADS
+#define PALD_PREP_THREADS 256
+#endif
+// The prep's per-row hashing is latency-bound: what counts is how many rows
+// are in flight per SM (shared memory and threads per CTA bound it).
+using TiePrep = TieConfig<PALD_PREP_THREADS, 2048, 512>;
 
-__global__ void __launch_bounds__(TieSmall::kThreads) batched_prep_kernel(const float* __restrict__ D,
+__global__ void __launch_bounds__(TiePrep::kThreads) batched_prep_kernel(const float* __restrict__ D,
                                                                           const MatrixDesc* __restrict__ mats,
                                                                           const PadDesc* __restrict__ pads,
                                                                           float* __restrict__ Dp,
                                                                           ScanResult* __restrict__ scans,
                                                                           uint32_t* __restrict__ tmaps, int count) {
-  __shared__ TieSmall::Smem sm;
+  __shared__ TiePrep::Smem sm;
   for (int m = blockIdx.y; m < count; m += gridDim.y) {
     const MatrixDesc md = mats[m];
     const PadDesc pd = pads[m];
@@ -150,9 +161,9 @@ __global__ void __launch_bounds__(TieSmall::kThreads) batched_prep_kernel(const 
       // prefetch per 128-byte line)
       const int64_t next = row + gridDim.x;
       if (next < md.n)
-        for (int64_t c = 32 * static_cast<int64_t>(threadIdx.x); c < md.n; c += 32 * TieSmall::kThreads)
+        for (int64_t c = 32 * static_cast<int64_t>(threadIdx.x); c < md.n; c += 32 * TiePrep::kThreads)
           asm volatile("prefetch.global.L2 [%0];" ::"l"(D + md.off + next * md.n + c));
-      tie_map_row<TieSmall>(D + md.off, md.n, row, tmaps + md.tmap_off, dm, sm,
+      tie_map_row<TiePrep>(D + md.off, md.n, row, tmaps + md.tmap_off, dm, sm,
                             PrepVisit{Dp + pd.off_p + row * pd.pitch, &inv_min, &mx});
     }
 #pragma unroll
@@ -214,8 +225,12 @@ __global__ void __launch_bounds__(FG::NT, 3) batched_focus_kernel(const float* _
     const MatrixDesc md = mats[w.matrix];
     const PadDesc pd = pads[w.matrix];
     const float scale = focus_scale(scans[w.matrix].inv_min_pos_bits);
-    if (!focus_tile_tma<FG>(maps + 2 * w.matrix, D + md.off, md.n, U + md.off, w.a, w.b, scale, md.n % 4 == 0,
-                            ring, Rp + pd.off_p, pd.pitch, w.kind == kItemTile)) {
+    const bool ok = w.kind == kItemDiagPair
+                        ? focus_diag_pair_tma<FG>(maps + 2 * w.matrix, D + md.off, md.n, U + md.off, w.a, w.b, scale,
+                                                  md.n % 4 == 0, ring, Rp + pd.off_p, pd.pitch)
+                        : focus_tile_tma<FG>(maps + 2 * w.matrix, D + md.off, md.n, U + md.off, w.a, w.b, scale,
+                                             md.n % 4 == 0, ring, Rp + pd.off_p, pd.pitch, false);
+    if (!ok) {
       if (threadIdx.x == 0) atomicOr(&g_batched_faults, 1u);
       break;
     }
@@ -244,12 +259,42 @@ __global__ void __launch_bounds__(CG::NT, 2) batched_cohesion_kernel(const float
     const WorkItem w = items[it];
     const MatrixDesc md = mats[w.matrix];
     const float S = focus_scale(scans[w.matrix].inv_min_pos_bits);
-    if (!cohesion_tile_tma<CG, MODE>(maps + 2 * w.matrix, maps + 2 * w.matrix + 1, D + md.off, md.n, C + md.off,
-                                     tmaps + md.tmap_off, S, w.a, w.b, md.n % 4 == 0, ring, tie_words,
-                                     w.kind == kItemTile)) {
+    // One call site for every tile.  Pass 2 takes a pair item's diagonal
+    // tiles one after the other, four warps each (the in-group pairs are the
+    // group kernel's): on the two halves of one CTA, as pass 1 does, it
+    // measured no faster, and the second tile function raised register spills.
+    bool ok = true;
+    const bool pair = w.kind == kItemDiagPair;
+    const int nsub = pair && w.b >= 0 ? 2 : 1;
+    for (int h = 0; h < nsub && ok; ++h) {
+      const int bi = pair && h == 1 ? w.b : w.a;
+      ok = cohesion_tile_tma<CG, MODE>(maps + 2 * w.matrix, maps + 2 * w.matrix + 1, D + md.off, md.n, C + md.off,
+                                       tmaps + md.tmap_off, S, bi, pair ? bi : w.b, md.n % 4 == 0, ring, tie_words,
+                                       pair);
+    }
+    if (!ok) {
       if (threadIdx.x == 0) atomicOr(&g_batched_faults, 1u);
       break;
     }
+  }
+}
+
+// Pass 1's pairs inside each group of four points, which paired diagonal
+// tiles leave out: one thread per group (focus_group), the listed matrices
+// along blockIdx.y, groups along x.  Runs after the pass-1 tiles, before
+// pass 2 reads R.
+__global__ void __launch_bounds__(kGroupThreads) batched_focus_group_kernel(
+    int32_t* __restrict__ U, const float* __restrict__ Dp, float* __restrict__ Rp,
+    const MatrixDesc* __restrict__ mats, const PadDesc* __restrict__ pads, const ScanResult* __restrict__ scans,
+    const int32_t* __restrict__ order, int count) {
+  for (int k = blockIdx.y; k < count; k += gridDim.y) {
+    const int m = order[k];
+    const MatrixDesc md = mats[m];
+    const int64_t q = int64_t(blockIdx.x) * kGroupThreads + threadIdx.x;
+    if (4 * q >= md.n) continue;
+    const PadDesc pd = pads[m];
+    focus_group(Dp + pd.off_p, pd.pitch, md.n, q, focus_scale(scans[m].inv_min_pos_bits), U + md.off,
+                Rp + pd.off_p, pd.pitch);
   }
 }
 
@@ -257,8 +302,6 @@ __global__ void __launch_bounds__(CG::NT, 2) batched_cohesion_kernel(const float
 // tiles leave out: one thread per group, the listed matrices along
 // blockIdx.y (largest first), groups along x.  Reads the padded copies of D
 // and R.
-constexpr int kGroupThreads = 128;
-
 template <int MODE>
 __global__ void __launch_bounds__(kGroupThreads, 3) batched_cohesion_group_kernel(
     float* __restrict__ C, const float* __restrict__ Dp, const float* __restrict__ Rp,
@@ -365,10 +408,17 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
   for (int i : order) {
     ScheduleBucket sb;
     schedule_for(ns[i], &sb);
-    const int32_t kind = sb.batched_split ? kItemTile : kItemTileWhole;
     const int T = static_cast<int>((ns[i] + kB - 1) / kB);
     for (int bi = 0; bi < T; ++bi)
       for (int bj = bi; bj < T; ++bj) {
+        if (bi == bj && sb.batched_split) {
+          if (bi % 2 == 1) continue;  // taken with bi - 1
+          const WorkItem w{i, bi, bi + 1 < T ? bi + 1 : -1, kItemDiagPair};
+          items1.push_back(w);
+          items2.push_back(w);
+          continue;
+        }
+        const int32_t kind = sb.batched_split ? kItemTile : kItemTileWhole;
         items1.push_back(WorkItem{i, bi, bj, kind});
         items2.push_back(WorkItem{i, bi, bj, kind});
       }
@@ -472,10 +522,13 @@ pald_status build_plan(int32_t count, const int64_t* ns, const int64_t* offs, co
       batched_copy_kernel<<<dim3(kCopyBlocksPerMatrix, gy), kCopyThreads, 0, cs>>>(D, d_mats, d_pads, d_dpad,
                                                                                     d_scans, count);
     else
-      batched_prep_kernel<<<dim3(kTieBlocksPerMatrix, gy), TieSmall::kThreads, 0, cs>>>(D, d_mats, d_pads, d_dpad,
+      batched_prep_kernel<<<dim3(kTieBlocksPerMatrix, gy), TiePrep::kThreads, 0, cs>>>(D, d_mats, d_pads, d_dpad,
                                                                                         d_scans, d_tmaps, count);
     batched_focus_kernel<<<gf, FG::NT, fsmem, cs>>>(D, U, d_rpad, d_mats, d_pads, d_scans, d_maps, d_items1, n1,
                                                     d_counters);
+    if (ng > 0)
+      batched_focus_group_kernel<<<ggrid, kGroupThreads, 0, cs>>>(U, d_dpad, d_rpad, d_mats, d_pads, d_scans,
+                                                                  d_order, ng);
     if (plain) {
       batched_cohesion_kernel<PALD_ACCUM_PLAIN><<<gc, CG::NT, csmem, cs>>>(D, C, d_mats, d_scans, d_tmaps, d_maps,
                                                                           d_items2, n2, d_counters + 1);
@@ -546,6 +599,19 @@ pald_status pald_batched(int32_t count, const int64_t* n_host, const int64_t* of
       pald_status st = pald_validate(D + off_host[i], n_host[i], stream);
       if (st != PALD_OK) return st;
     }
+  }
+  if (o.accum_mode == PALD_ACCUM_FIXED) {
+    // exact integer sums: the matrices go one after another through the
+    // single-matrix path (the same bits as pald_focus + pald_cohesion)
+    pald_opts o1 = o;
+    o1.validate = 0;
+    o1.schedule_id = -1;
+    for (int i = 0; i < count; ++i) {
+      pald_status st = pald_focus(D + off_host[i], n_host[i], U + off_host[i], &o1, stream);
+      if (st == PALD_OK) st = pald_cohesion(D + off_host[i], U + off_host[i], n_host[i], C + off_host[i], &o1, stream);
+      if (st != PALD_OK) return st;
+    }
+    return PALD_OK;
   }
   int device = 0;
   cudaError_t e = cudaGetDevice(&device);

@@ -224,6 +224,12 @@ cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s);
 cudaError_t take_focus_faults(uint32_t* out, cudaStream_t s);
 cudaError_t take_batched_faults(uint32_t* out, cudaStream_t s);
 cudaError_t take_pairwise_faults(uint32_t* out, cudaStream_t s);
+cudaError_t take_fixed_faults(uint32_t* out, cudaStream_t s);
+// Fixed-point pass 2 (PALD_ACCUM_FIXED) on the upper-triangle tiles
+// [t0, t1) (t1 < 0: all), with `scratch` of fixed_scratch_bytes(D, n) bytes.
+size_t fixed_scratch_bytes(const float* D, int64_t n);
+cudaError_t launch_fixed_cohesion(const float* D, const int32_t* U, int64_t n, float* C, const uint32_t* tmap,
+                                  const ScanResult* scan, void* scratch, int64_t t0, int64_t t1, cudaStream_t s);
 // One CTA whose bounded waits run out after limit_ns (the give-up path of
 // the TMA pipeline); it records the pass-2 fault word.
 cudaError_t launch_wait_selftest(uint64_t limit_ns, cudaStream_t s);
@@ -245,13 +251,15 @@ struct MatrixDesc {
 };
 struct WorkItem {
   int32_t matrix;
-  int32_t a, b;  // block row and column of the tile (a <= b)
-  int32_t kind;  // kItemTile or kItemTileWhole
+  int32_t a, b;  // block row and column of the tile (a <= b); for kItemDiagPair the two diagonal blocks
+  int32_t kind;  // kItemTile, kItemTileWhole or kItemDiagPair
 };
 enum : int32_t {
-  kItemTile = 0,       // one 64 x 64 upper-triangle tile; a diagonal one leaves its in-group pairs
-                       // (x / 4 == z / 4) to other warps (pass 1) or to the group kernel (pass 2)
-  kItemTileWhole = 1,  // as kItemTile, but a diagonal tile computes all of its pairs itself
+  kItemTile = 0,       // one 64 x 64 upper-triangle tile off the diagonal
+  kItemTileWhole = 1,  // one 64 x 64 upper-triangle tile; a diagonal one computes all of its pairs
+  kItemDiagPair = 2,   // diagonal tiles (a, a) and (b, b) of one matrix (b < 0: only a): pass 1
+                       // runs them on the two halves of a CTA, pass 2 one after the other;
+                       // their in-group pairs (x / 4 == z / 4) come from the group kernels
 };
 
 }  // namespace pald

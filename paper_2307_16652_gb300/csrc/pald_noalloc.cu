@@ -64,6 +64,7 @@ extern "C" pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, i
                                              const pald_opts* opts, pald_stream_t stream) {
   if (!D || !U || !C || n < 2 || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
   if (opts && (opts->flags & PALD_FLAG_IGNORE_TIES)) return PALD_ERR_INVALID_ARG;  // needs a tie map
+  if (opts && opts->accum_mode == PALD_ACCUM_FIXED) return PALD_ERR_INVALID_ARG;    // needs two weight arrays
   if (n > kNoAllocMaxN) return PALD_ERR_UNSUPPORTED;  // R would not fit the fixed array
   const pald_opts o = opts_or_default(opts);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

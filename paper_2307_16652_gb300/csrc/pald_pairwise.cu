@@ -320,6 +320,7 @@ int64_t pald_pairwise_scratch_bytes(int64_t n) {
 
 pald_status pald_pairwise(const float* D, int64_t n, float* C, const pald_opts* opts, pald_stream_t stream) {
   if (!D || !C || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
+  if (opts && opts->accum_mode == PALD_ACCUM_FIXED) return PALD_ERR_INVALID_ARG;  // compensated or plain only
   if (reinterpret_cast<uintptr_t>(D) % 16 || reinterpret_cast<uintptr_t>(C) % 16) return PALD_ERR_INVALID_ARG;
   const pald_opts o = opts_or_default(opts);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -23,6 +23,8 @@ pald_status cuda_fail(cudaError_t e);
 bool opts_ok(const pald_opts* o);
 pald_opts opts_or_default(const pald_opts* o);
 pald_status scan_and_check(const float* D, int64_t n, ScanResult* scratch, bool validate, cudaStream_t s);
+pald_status cohesion_fixed(const float* D, const int32_t* U, int64_t n, float* C, const pald_opts& o, int64_t t0,
+                           int64_t t1, cudaStream_t s);
 
 namespace {
 
@@ -135,6 +137,7 @@ pald_status pald_cohesion_tiles(const float* D, const int32_t* U, int64_t n, int
   if (!D || !U || !C || n < 2 || n > kMaxN || !opts_ok(opts) || !range_ok(n, t0, t1)) return PALD_ERR_INVALID_ARG;
   const pald_opts o = opts_or_default(opts);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (o.accum_mode == PALD_ACCUM_FIXED) return cohesion_fixed(D, U, n, C, o, t0, t1, s);
   const size_t rbytes = static_cast<size_t>(n) * static_cast<size_t>(n) * sizeof(float);
   const size_t tbytes = (static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t) + 255) / 256 * 256;
   Scratch scratch(s);
