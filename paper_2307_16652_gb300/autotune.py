@@ -12,7 +12,8 @@ the fastest schedule of each pass at its order.
 For the buckets within the batched range (orders up to 4096) it then times
 ``pald_batched`` on a set of batched-recipe matrices whose orders fall in the
 bucket, once with diagonal tiles splitting off their in-group pairs and once
-without, checks that both give the same bits, and keeps the faster.
+without, checks that both give the same bits, and keeps the split unless the
+whole tiles are faster by more than 1% (``choose_split``).
 
 The result is one table keyed by GPU name and SM count.  ``--install``
 merges it into ``tuned_schedules.json`` beside this file, from which
@@ -113,6 +114,24 @@ def batched_set(lo, hi, work, seed):
     return ns, offs, D
 
 
+SPLIT_MARGIN = 0.01  # the whole-tile choice must win by more than this fraction (measurement noise)
+
+
+def choose_split(ms_split: float, ms_whole: float) -> int:
+    """Keep the default (diagonal tiles split, in pairs) unless whole tiles
+    are faster by more than SPLIT_MARGIN: a bucket's test set is a small
+    sample of the orders, and on the full batched workload a choice within
+    noise on its bucket set measured slower."""
+    return 0 if ms_whole < ms_split * (1.0 - SPLIT_MARGIN) else 1
+
+
+def rederive(table):
+    """Re-apply choose_split to a table's own batched measurements."""
+    for m in table.get("measured", {}).get("batched", []):
+        table["buckets"][m["bucket"]]["batched_split"] = choose_split(m["ms_split"], m["ms_whole"])
+    return table
+
+
 def tune_batched(buckets, reps, work, log):
     import torch
 
@@ -139,7 +158,7 @@ def tune_batched(buckets, reps, work, log):
             binding.pald_release()
         if not (torch.equal(bits[0][0], bits[1][0]) and torch.equal(bits[0][1], bits[1][1])):
             raise RuntimeError(f"batched split and whole diagonal tiles differ in bucket {k}")
-        b["batched_split"] = 1 if ms[1] <= ms[0] else 0
+        b["batched_split"] = choose_split(ms[1], ms[0])
         results.append({"bucket": k, "orders": [int(ns.min()), int(ns.max())], "matrices": len(ns),
                         "ms_split": round(ms[1], 4), "ms_whole": round(ms[0], 4)})
         log(f"batched bucket {k} (n {lo}..{hi}, {len(ns)} matrices): split {ms[1]:.3f} ms, whole {ms[0]:.3f} ms")
