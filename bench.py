@@ -390,6 +390,17 @@ def run_other_workloads(props, sm_max):
     n = 8192
     D = inputs.euclidean_fp32_torch(inputs.paper_points(n), "cuda")
     C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    U = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    L = torch.empty(n, dtype=torch.float32, device="cuda")
+    pald.pald_focus(D, U)
+    ms_c = timed(lambda: pald.pald_cohesion(D, U, C), 2)
+    ms_sep = timed(lambda: pald.pald_local_depth(C, L), 5)
+    ms_f = timed(lambda: pald.pald_cohesion_depth(D, U, C, L), 2)
+    out["depth-paper-8192"] = {"n": n, "cohesion_ms": round(ms_c, 3), "cohesion_depth_ms": round(ms_f, 3),
+                               "local_depth_pass_ms": round(ms_sep, 3),
+                               "note": "pass 2 with the row sums in its epilogue vs pass 2 alone and the "
+                                       "separate O(n^2) pass over C"}
+    del U, L
     ms = timed(lambda: pald.pald_pairwise(D, C), 2)
     out["pairwise-paper-8192"] = {"n": n, "ms_both_passes": round(ms, 3),
                                   "triplets_per_s_per_pass": 2 * triplets(n) / (ms / 1e3) / 2,

@@ -124,6 +124,26 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
                           const pald_opts* opts, pald_stream_t stream);
 
 /*
+ * pald_cohesion_depth - pass 2 with the local depths fused into its
+ * epilogue (Sec. 2: the cohesion of x partitions its local depth, eq. (LD),
+ * so l_x is the sum of row x of C).
+ *   D, U, C, opts  as pald_cohesion; C receives the same bits.
+ *   L  device, n FP32, written completely: L[x] = sum over z of c_xz, the
+ *      sum of the stored FP32 entries of row x of C.
+ * Each 64 x 64 tile sums, in a fixed order and in FP64, the entries it
+ * stores into a per-tile partial (scratch of 8 * n * ceil(n / 64) bytes); a
+ * last kernel adds each row's partials in block order and rounds once to
+ * FP32.  The result does not depend on timing.  This needs the TMA layout
+ * (n % 4 == 0, n >= 64, D and C 16-byte aligned), an automatic schedule or
+ * schedule 7 and a floating-point accum_mode; otherwise L comes from
+ * pald_local_depth on C after pald_cohesion (the same sum up to the last
+ * rounding).
+ * Errors: as pald_cohesion; INVALID_ARG also for a null L.
+ */
+pald_status pald_cohesion_depth(const float* D, const int32_t* U, int64_t n, float* C, float* L,
+                                const pald_opts* opts, pald_stream_t stream);
+
+/*
  * pald_batched - both passes for `count` independent matrices of uneven order
  * in one persistent launch per pass, replayed from a cached CUDA graph.
  *   count     number of matrices, 1 <= count <= 2^20.

@@ -25,6 +25,7 @@ from .binding import (  # noqa: F401
     library_path,
     pald_batched,
     pald_cohesion,
+    pald_cohesion_depth,
     pald_cohesion_noalloc,
     pald_cohesion_tiles,
     pald_focus,
@@ -53,7 +54,7 @@ from .binding import (  # noqa: F401
 
 __all__ = [
     "PALD_ACCUM_COMPENSATED", "PALD_ACCUM_FIXED", "PALD_ACCUM_PLAIN", "PALD_FLAG_IGNORE_TIES", "PaldError", "lib", "library_path", "pald_check_faults",
-    "pald_batched", "pald_cohesion", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_local_depth",
+    "pald_batched", "pald_cohesion", "pald_cohesion_depth", "pald_cohesion_noalloc", "pald_focus", "pald_host", "pald_local_depth",
     "pald_release", "pald_strong_ties", "pald_test_bounded_wait",
     "pald_schedule_count", "pald_schedule_name", "pald_set_schedule_table", "pald_get_schedule", "pald_status_string", "pald_tie_map", "pald_tie_map_words",
     "pald_validate", "pald_version", "pald_cohesion_tiles", "pald_focus_tiles", "pald_pack_tiles",

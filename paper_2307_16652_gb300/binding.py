@@ -69,6 +69,7 @@ def _lib() -> ctypes.CDLL:
         h.pald_focus.argtypes = [vp, i64, vp, op, vp]
         h.pald_cohesion.argtypes = [vp, vp, i64, vp, op, vp]
         h.pald_cohesion_noalloc.argtypes = [vp, vp, i64, vp, op, vp]
+        h.pald_cohesion_depth.argtypes = [vp, vp, i64, vp, vp, op, vp]
         h.pald_batched.argtypes = [i32, vp, vp, vp, vp, vp, op, vp]
         h.pald_host.argtypes = [vp, i64, vp, vp, op]
         h.pald_validate.argtypes = [vp, i64, vp]
@@ -91,7 +92,8 @@ def _lib() -> ctypes.CDLL:
         h.pald_strong_ties.argtypes = [vp, i64, ctypes.c_float, vp, vp]
         h.pald_tie_map_words.argtypes = [i64]
         h.pald_tie_map_words.restype = i64
-        for f in (h.pald_focus, h.pald_cohesion, h.pald_cohesion_noalloc, h.pald_batched, h.pald_host,
+        for f in (h.pald_focus, h.pald_cohesion, h.pald_cohesion_noalloc, h.pald_cohesion_depth, h.pald_batched,
+                  h.pald_host,
                   h.pald_validate, h.pald_tie_map, h.pald_check_faults, h.pald_local_depth, h.pald_strong_ties,
                   h.pald_test_bounded_wait, h.pald_set_schedule_table, h.pald_get_schedule, h.pald_shard_range,
                   h.pald_focus_tiles, h.pald_cohesion_tiles, h.pald_pack_tiles, h.pald_unpack_tiles,
@@ -175,6 +177,26 @@ def pald_cohesion(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED,
                               _check(C, torch.float32, n, "C"), ctypes.byref(o), _stream_ptr(stream))
     _raise(st, "pald_cohesion")
     return C
+
+
+def pald_cohesion_depth(D, U, C, L=None, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1,
+                        ignore_ties=False, stream=None):
+    """Pass 2 with the local depths L[x] = sum_z C[x, z] from its epilogue;
+    returns (C, L).  C gets the same bits as :func:`pald_cohesion`."""
+    import torch
+
+    n = D.shape[0]
+    if L is None:
+        L = torch.empty(n, dtype=torch.float32, device=D.device)
+    if not (isinstance(L, torch.Tensor) and L.is_cuda and L.dtype == torch.float32 and L.is_contiguous()
+            and tuple(L.shape) == (n,)):
+        raise ValueError(f"L must be a contiguous float32 CUDA tensor of shape ({n},)")
+    o = _opts(validate, accum_mode, schedule_id, ignore_ties)
+    st = _lib().pald_cohesion_depth(_check(D, torch.float32, n, "D"), _check(U, torch.int32, n, "U"), n,
+                                    _check(C, torch.float32, n, "C"), L.data_ptr(), ctypes.byref(o),
+                                    _stream_ptr(stream))
+    _raise(st, "pald_cohesion_depth")
+    return C, L
 
 
 def pald_cohesion_noalloc(D, U, C, *, validate=False, accum_mode=PALD_ACCUM_COMPENSATED, schedule_id=-1,

@@ -201,14 +201,13 @@ __device__ __forceinline__ void cohesion_stage(const float* ad, const float* ar,
         lds<Geo::CW>(br + kk * Geo::BY + Geo::col_off(tz, Geo::CW * g), r2 + Geo::CW * g);
       }
 #pragma unroll
-      for (int i = 0; i < TX; ++i)
-#pragma unroll
-        for (int j = 0; j < TY; ++j) {
-          if (SHORT)
-            cohesion_step_short(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
-          else
-            cohesion_step(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
-        }
+      for (int q = 0; q < TX * TY; ++q) {
+        const int i = q / TY, j = q % TY;
+        if (SHORT)
+          cohesion_step_short(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
+        else
+          cohesion_step(sacc[i][j], a1[i], a2[j], S, cv[i][j], r1[i], r2[j]);
+      }
       if (MODE == PALD_ACCUM_COMPENSATED) {
         // pair (x, z) folds after the y with y mod kMergeEvery ==
         // fold_phase(i, j) (k0 and every stage start are multiples of
@@ -222,6 +221,119 @@ __device__ __forceinline__ void cohesion_stage(const float* ad, const float* ar,
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Packed stage of the 64 x 64 TMA tile (4 x 4 pairs per thread).  The
+// partials of pairs (i, j) and (i, j + 2) fold at the same y (x + z keeps
+// its parity), so they share one 64-bit register per side:
+//   sx[i][jj] = {S_xz(i, jj), S_xz(i, jj + 2)},  sz[i][jj] = {S_zx(i, jj), S_zx(i, jj + 2)}
+// (hx, hz the same for H).  The short form then credits both pairs of a
+// side with one packed FMA: 3 issue slots per pair instead of 4, with the
+// same FMA-pipe work.  Every lane performs exactly the FMA of the scalar
+// form, so the bits do not change.  The R panels must hold the columns of
+// each group of four in the order 0, 2, 1, 3 (reciprocal_rows with
+// `paired`): {r_zy(jj), r_zy(jj + 2)} is then one aligned register pair,
+// and {r_xy, r_xy} costs one move per row slot and y.
+
+// Short form of pairs (i, jj) and (i, jj + 2).
+__device__ __forceinline__ void cohesion_step2_short(uint64_t& sx, uint64_t& sz, float a1, float a2lo, float a2hi,
+                                                     float S, float clo, float chi, uint64_t r1d, uint64_t r2p) {
+  asm("{\n\t.reg .f32 m0, m1, v0, v1;\n\t.reg .b64 v;\n\t"
+      "min.f32 m0, %2, %3;\n\t"
+      "min.f32 m1, %2, %4;\n\t"
+      "fma.rn.sat.f32 v0, m0, %5, %6;\n\t"
+      "fma.rn.sat.f32 v1, m1, %5, %7;\n\t"
+      "mov.b64 v, {v0, v1};\n\t"
+      "fma.rn.f32x2 %0, v, %8, %0;\n\t"
+      "fma.rn.f32x2 %1, v, %9, %1;\n\t}"
+      : "+l"(sx), "+l"(sz)
+      : "f"(a1), "f"(a2lo), "f"(a2hi), "f"(S), "f"(clo), "f"(chi), "l"(r1d), "l"(r2p));
+}
+
+// Long form of one pair on lane L of the packed partials (cohesion_step).
+template <int L>
+__device__ __forceinline__ void cohesion_step2_long(uint64_t& sx, uint64_t& sz, float a1, float a2, float S, float c,
+                                                    float r1, float r2) {
+  float x0, x1, z0, z1;
+  unpack2(sx, x0, x1);
+  unpack2(sz, z0, z1);
+  uint64_t p = L == 0 ? pack2(x0, z0) : pack2(x1, z1);
+  cohesion_step(p, a1, a2, S, c, r1, r2);
+  float px, pz;
+  unpack2(p, px, pz);
+  sx = L == 0 ? pack2(px, x1) : pack2(x0, px);
+  sz = L == 0 ? pack2(pz, z1) : pack2(z0, pz);
+}
+
+template <class Geo, int MODE, bool SHORT>
+__device__ __forceinline__ void cohesion_stage_packed(const float* ad, const float* ar, const float* bd,
+                                                      const float* br, int tx, int tz, float S,
+                                                      const float (&cv)[4][4], uint64_t (&sx)[4][2],
+                                                      uint64_t (&sz)[4][2], uint64_t (&hx)[4][2],
+                                                      uint64_t (&hz)[4][2], int kend) {
+  static_assert(Geo::TX == 4 && Geo::TY == 4 && Geo::GX == 1 && Geo::GY == 1 && Geo::BX == 64 && Geo::BY == 64,
+                "the packed stage is for 64 x 64 tiles with 4 x 4 pairs per thread");
+  constexpr int kSlot[4] = {0, 2, 1, 3};  // register of r_xy(i) in the paired order
+#pragma unroll 1
+  for (int k0 = 0; k0 < kend; k0 += Geo::UNR) {
+#pragma unroll
+    for (int k = 0; k < Geo::UNR; ++k) {
+      const int kk = k0 + k;
+      float a1[4], rx[4], a2[4];
+      lds<4>(ad + kk * 64 + 4 * tx, a1);
+      lds<4>(ar + kk * 64 + 4 * tx, rx);
+      lds<4>(bd + kk * 64 + 4 * tz, a2);
+      const ulonglong2 rz = *reinterpret_cast<const ulonglong2*>(br + kk * 64 + 4 * tz);
+      const uint64_t r2p[2] = {rz.x, rz.y};  // {r_zy(0), r_zy(2)}, {r_zy(1), r_zy(3)}
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float r1 = rx[kSlot[i]];
+        if (SHORT) {
+          const uint64_t r1d = pack2(r1, r1);
+#pragma unroll
+          for (int jj = 0; jj < 2; ++jj)
+            cohesion_step2_short(sx[i][jj], sz[i][jj], a1[i], a2[jj], a2[jj + 2], S, cv[i][jj], cv[i][jj + 2], r1d,
+                                 r2p[jj]);
+        } else {
+#pragma unroll
+          for (int jj = 0; jj < 2; ++jj) {
+            float r2lo, r2hi;
+            unpack2(r2p[jj], r2lo, r2hi);
+            cohesion_step2_long<0>(sx[i][jj], sz[i][jj], a1[i], a2[jj], S, cv[i][jj], r1, r2lo);
+            cohesion_step2_long<1>(sx[i][jj], sz[i][jj], a1[i], a2[jj + 2], S, cv[i][jj + 2], r1, r2hi);
+          }
+        }
+      }
+      if (MODE == PALD_ACCUM_COMPENSATED) {
+        // the fold points of cohesion_stage: pairs (i, jj) and (i, jj + 2) share fold_phase(i, jj)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int jj = 0; jj < 2; ++jj)
+            if ((k % kMergeEvery) == fold_phase(i, jj)) {
+              fast2sum_fold(hx[i][jj], sx[i][jj]);
+              fast2sum_fold(hz[i][jj], sz[i][jj]);
+            }
+      }
+    }
+  }
+}
+
+// The packed partials of cohesion_stage_packed back in the per-pair layout
+// {xz, zx} of cohesion_finish.
+__device__ __forceinline__ void unpair_partials(const uint64_t (&sx)[4][2], const uint64_t (&sz)[4][2],
+                                                uint64_t (&acc)[4][4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      float x0, x1, z0, z1;
+      unpack2(sx[i][jj], x0, x1);
+      unpack2(sz[i][jj], z0, z1);
+      acc[i][jj] = pack2(x0, z0);
+      acc[i][jj + 2] = pack2(x1, z1);
+    }
 }
 
 // Reads the tie-map row of one tile's block pair: tied(st) is nonzero when
@@ -292,12 +404,16 @@ __device__ __forceinline__ float cohesion_value(uint64_t h2, uint64_t s2, bool z
   return mul_pair(s, 0.f, ih, il);
 }
 
-// Final merge and stores of C[X, Z] (and of C[Z, X] when `mirror`).
-template <class Geo, int MODE>
+// Final merge and stores of C[X, Z] (and of C[Z, X] when `mirror`).  With
+// DEPTH, rs[i] also receives the sum (in FP64, in column order) of the
+// stored values of row X0 + row_off(tx, i) inside the matrix, and ms[j]
+// that of mirror row Z0 + col_off(tz, j); both start at 0.
+template <class Geo, int MODE, bool DEPTH = false>
 __device__ __forceinline__ void cohesion_finish(float* __restrict__ C, int64_t n, int64_t X0, int64_t Z0, int tx,
                                                 int tz, bool mirror, bool vec,
                                                 const uint64_t (&sacc)[Geo::TX][Geo::TY],
-                                                const uint64_t (&hacc)[Geo::TX][Geo::TY]) {
+                                                const uint64_t (&hacc)[Geo::TX][Geo::TY],
+                                                double (*rs)[Geo::TX] = nullptr, double (*ms)[Geo::TY] = nullptr) {
   float ih, il;
   inverse_pair(n - 1, ih, il);
   auto finish = [&](uint64_t h2, uint64_t s2, bool zx) -> float { return cohesion_value<MODE>(h2, s2, zx, ih, il); };
@@ -309,7 +425,13 @@ __device__ __forceinline__ void cohesion_finish(float* __restrict__ C, int64_t n
       float v[Geo::CW];
 #pragma unroll
       for (int k = 0; k < Geo::CW; ++k) v[k] = finish(hacc[i][Geo::CW * gj + k], sacc[i][Geo::CW * gj + k], false);
-      storew<Geo::CW>(C, n, x, Z0 + Geo::col_off(tz, Geo::CW * gj), v, vec);
+      const int64_t z0 = Z0 + Geo::col_off(tz, Geo::CW * gj);
+      storew<Geo::CW>(C, n, x, z0, v, vec);
+      if constexpr (DEPTH) {
+#pragma unroll
+        for (int k = 0; k < Geo::CW; ++k)
+          if (x < n && z0 + k < n) (*rs)[i] += static_cast<double>(v[k]);
+      }
     }
   }
   if (mirror) {
@@ -321,7 +443,13 @@ __device__ __forceinline__ void cohesion_finish(float* __restrict__ C, int64_t n
         float v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = finish(hacc[4 * gi + k][j], sacc[4 * gi + k][j], true);
-        storew<4>(C, n, z, X0 + Geo::row_off(tx, 4 * gi), v, vec);
+        const int64_t x0 = X0 + Geo::row_off(tx, 4 * gi);
+        storew<4>(C, n, z, x0, v, vec);
+        if constexpr (DEPTH) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (z < n && x0 + k < n) (*ms)[j] += static_cast<double>(v[k]);
+        }
       }
     }
   }
@@ -414,17 +542,66 @@ struct CohesionTmaSmem {
   static constexpr int MAX_BYTES = Ring::BYTES + 128 + 4 * kTieWordsMax;
 };
 
+// Row sums of one finished 64 x 64 tile for the fused local depth (Sec. 2,
+// eq. (LD): l_x is the sum of row x of C).  P is [T][n] FP64 with T = the
+// number of 64-wide column blocks: P[bj * n + x] receives the sum of c_xz
+// over the tile's columns z (block bj) for each row x of X, and, off the
+// diagonal, P[bi * n + z] that of c_zx over block bi for each row z of Z.
+// Every entry of P is written by exactly one tile.  The order is fixed: a
+// thread's four columns (cohesion_finish), then the 16 column groups of
+// four in order.  `sh` holds 2 x 16 x 64 doubles of shared memory; all NT
+// threads call this together.
+template <class Geo>
+__device__ __forceinline__ void depth_partials(double* __restrict__ P, int64_t n, int bi, int bj, int tx, int tz,
+                                               bool active, bool mirror, const double (&rs)[Geo::TX],
+                                               const double (&ms)[Geo::TY], double* sh) {
+  static_assert(Geo::TX == 4 && Geo::TY == 4 && Geo::GX == 1 && Geo::GY == 1, "4 x 4 pairs per thread");
+  // SX[g][r]: columns 4g..4g+3 of row r of X.  On the diagonal the rows of
+  // Z are those of X, and block (a, b) with a < b writes row part (b, 4a+i)
+  // and mirror part (a, 4b+j): every (group, row) slot exactly once.
+  double* SX = sh;
+  double* SZ = bi == bj ? sh : sh + 16 * 64;
+  for (int k = threadIdx.x; k < 2 * 16 * 64; k += Geo::NT) sh[k] = 0.0;  // groups past n stay 0
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) SX[tz * 64 + 4 * tx + i] = rs[i];
+    if (mirror) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) SZ[tx * 64 + 4 * tz + j] = ms[j];
+    }
+  }
+  __syncthreads();
+  const int t = static_cast<int>(threadIdx.x);
+  const bool zpart = t >= 64;
+  if (t < 128 && !(zpart && bi == bj)) {
+    const double* S = zpart ? SZ : SX;
+    const int r = t & 63;
+    const int64_t row = int64_t(zpart ? bj : bi) * 64 + r;
+    if (row < n) {
+      double sum = 0.0;
+#pragma unroll
+      for (int g = 0; g < 16; ++g) sum += S[g * 64 + r];
+      P[int64_t(zpart ? bi : bj) * n + row] = sum;
+    }
+  }
+}
+
 // Returns false when a wait ran out of time; the CTA then stops early and
 // its outputs are unspecified.  `tie_words` holds tie_map_dims(n).wpp words
 // of shared memory.  With `skip_diag` a diagonal tile leaves out its 4 x 4
 // blocks on the diagonal (the pairs inside the groups of four points), for
-// cohesion_group below to compute: four warps instead of five.
-template <class Geo, int MODE>
+// cohesion_group below to compute: four warps instead of five.  With DEPTH
+// (and no `skip_diag`) the tile also writes its row sums to P
+// (depth_partials), reusing the ring's panels once the last stage is done.
+// With PACKED the stages run cohesion_stage_packed, which needs tmR to map
+// an R in the paired column order (the result is the same).
+template <class Geo, int MODE, bool DEPTH = false, bool PACKED = false>
 __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const CUtensorMap* tmR,
                                                   const float* __restrict__ D, int64_t n, float* __restrict__ C,
                                                   const uint32_t* __restrict__ tmap, float S, int bi, int bj,
                                                   bool vec, TmaRing<4, Geo::BK>& ring, uint32_t* tie_words,
-                                                  bool skip_diag = false) {
+                                                  bool skip_diag = false, double* __restrict__ P = nullptr) {
   constexpr int BK = Geo::BK, TX = Geo::TX, TY = Geo::TY, NT = Geo::NT;
   static_assert(Geo::BX == 64 && Geo::BY == 64 && Geo::TPX == 16 && Geo::TPY == 16 && Geo::GX == 1 &&
                     Geo::GY == 1 && Geo::CW == 4,
@@ -450,6 +627,16 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
   float cv[TX][TY];
   uint64_t sacc[TX][TY], hacc[TX][TY];
   cohesion_init<Geo>(D, n, X0, int64_t(bj) * 64, tx, tz, S, cv, sacc, hacc);
+  uint64_t sx[4][2], sz[4][2], hx[4][2], hz[4][2];  // the packed partials (PACKED only)
+  if constexpr (PACKED) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        sx[i][jj] = sz[i][jj] = sacc[i][jj];
+        hx[i][jj] = hz[i][jj] = hacc[i][jj];
+      }
+  }
 
   constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
   const CUtensorMap* const maps[4] = {tmD, tmR, tmD, tmR};
@@ -460,19 +647,42 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
         if (!active) return;
         const int g = st * BK / kTieGroup;
         const int kend = stage_extent<BK, Geo::UNR>(n, st);
-        if ((tie_words[g >> 5] >> (g & 31)) & kGroupMask)
-          cohesion_stage<Geo, MODE, false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
-                                           ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, kend);
-        else
-          cohesion_stage<Geo, MODE, true>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
-                                          ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, kend);
+        const bool tied = (tie_words[g >> 5] >> (g & 31)) & kGroupMask;
+        if constexpr (PACKED) {
+          if (tied)
+            cohesion_stage_packed<Geo, MODE, false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
+                                                    ring.panel(buf, 3), tx, tz, S, cv, sx, sz, hx, hz, kend);
+          else
+            cohesion_stage_packed<Geo, MODE, true>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
+                                                   ring.panel(buf, 3), tx, tz, S, cv, sx, sz, hx, hz, kend);
+        } else {
+          if (tied)
+            cohesion_stage<Geo, MODE, false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
+                                             ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, kend);
+          else
+            cohesion_stage<Geo, MODE, true>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
+                                            ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, kend);
+        }
       });
   __syncthreads();
   if (threadIdx.x == 0) ring.inval();
+  if constexpr (PACKED) {
+    unpair_partials(sx, sz, sacc);
+    unpair_partials(hx, hz, hacc);
+  }
   // off the diagonal, or for an above-diagonal block of a diagonal tile,
   // the block's mirror (the zx lanes) is written too
-  if (ok && active)
-    cohesion_finish<Geo, MODE>(C, n, X0, int64_t(bj) * 64, tx, tz, tx != tz || bi != bj, vec, sacc, hacc);
+  const bool mirror = tx != tz || bi != bj;
+  if constexpr (DEPTH) {
+    static_assert(Geo::BK * 64 * 4 * kTmaStages >= 2 * 16 * 64 * 2, "row sums fit in the ring's panels");
+    double rs[TX] = {}, ms[TY] = {};
+    if (ok && active) cohesion_finish<Geo, MODE, true>(C, n, X0, int64_t(bj) * 64, tx, tz, mirror, vec, sacc, hacc,
+                                                       &rs, &ms);
+    // every copy has landed and every stage has been read: the panels are free
+    if (ok) depth_partials<Geo>(P, n, bi, bj, tx, tz, active, mirror, rs, ms, reinterpret_cast<double*>(ring.panels));
+  } else {
+    if (ok && active) cohesion_finish<Geo, MODE>(C, n, X0, int64_t(bj) * 64, tx, tz, mirror, vec, sacc, hacc);
+  }
   return ok;
 }
 
@@ -608,8 +818,10 @@ __device__ __forceinline__ void cohesion_group(const float* __restrict__ Dp, con
 // R[row][col] = 1/u (correctly rounded FP32), 0 on the diagonal and where
 // u <= 0, for one row of an n x n matrix; U has row pitch n, R row pitch
 // `rp` (a multiple of 4 when `vec`).  The CTA's threads share the row.
+// With `paired` (n % 4 == 0) the columns of each group of four are stored
+// in the order 0, 2, 1, 3: the layout the packed pass-2 stage reads.
 __device__ __forceinline__ void reciprocal_rows(const int32_t* __restrict__ U, int64_t n, float* __restrict__ R,
-                                                int64_t rp, int64_t row, bool vec) {
+                                                int64_t rp, int64_t row, bool vec, bool paired = false) {
   const int32_t* u = U + row * n;
   float* r = R + row * rp;
   if (vec) {
@@ -622,12 +834,19 @@ __device__ __forceinline__ void reciprocal_rows(const int32_t* __restrict__ U, i
       o.y = (q.y <= 0 || c + 1 == row) ? 0.f : __frcp_rn(static_cast<float>(q.y));
       o.z = (q.z <= 0 || c + 2 == row) ? 0.f : __frcp_rn(static_cast<float>(q.z));
       o.w = (q.w <= 0 || c + 3 == row) ? 0.f : __frcp_rn(static_cast<float>(q.w));
+      if (paired) {
+        const float t = o.y;
+        o.y = o.z;
+        o.z = t;
+      }
       reinterpret_cast<float4*>(r)[k] = o;
     }
   } else {
     for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
       const int32_t q = __ldg(u + c);
-      r[c] = (q <= 0 || c == row) ? 0.f : __frcp_rn(static_cast<float>(q));
+      const int64_t m = c & 3;
+      const int64_t to = paired && (m == 1 || m == 2) ? (c ^ 3) : c;  // 1 <-> 2 within the group
+      r[to] = (q <= 0 || c == row) ? 0.f : __frcp_rn(static_cast<float>(q));
     }
   }
 }

@@ -239,10 +239,43 @@ pald_status pald_cohesion(const float* D, const int32_t* U, int64_t n, float* C,
   else
     e = launch_tie_map(D, n, tmap, s);
   if (e != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_reciprocal(U, R, n, s)) != cudaSuccess) return cuda_fail(e);
-  if ((e = launch_cohesion(D, R, n, C, tmap, scan, o.accum_mode, o.schedule_id, s)) != cudaSuccess)
+  if ((e = launch_cohesion(D, U, R, n, C, tmap, scan, o.accum_mode, o.schedule_id, s)) != cudaSuccess)
     return cuda_fail(e);
   return PALD_OK;
+}
+
+pald_status pald_cohesion_depth(const float* D, const int32_t* U, int64_t n, float* C, float* L,
+                                const pald_opts* opts, pald_stream_t stream) {
+  if (!D || !U || !C || !L || n < 2 || n > kMaxN || !opts_ok(opts)) return PALD_ERR_INVALID_ARG;
+  const pald_opts o = opts_or_default(opts);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool fused = o.accum_mode != PALD_ACCUM_FIXED && (o.schedule_id < 0 || o.schedule_id == 7) &&
+                     cohesion_depth_fused_ok(D, C, n);
+  if (!fused) {  // the row sums from a separate pass over C
+    const pald_status st = pald_cohesion(D, U, n, C, opts, stream);
+    return st == PALD_OK ? pald_local_depth(C, n, L, stream) : st;
+  }
+  // scratch: R = 1/u, the tie map, the scan summary, the per-tile row sums
+  const size_t rbytes = static_cast<size_t>(n) * static_cast<size_t>(n) * sizeof(float);
+  const size_t tbytes = (static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t) + 255) / 256 * 256;
+  const size_t pbytes = static_cast<size_t>((n + 63) / 64) * static_cast<size_t>(n) * sizeof(double);
+  Scratch scratch(s);
+  cudaError_t e = scratch.alloc(rbytes + tbytes + pbytes + 256);
+  if (e != cudaSuccess) return cuda_fail(e);
+  char* base = static_cast<char*>(scratch.p);
+  float* R = reinterpret_cast<float*>(base);
+  auto* tmap = reinterpret_cast<uint32_t*>(base + rbytes);
+  auto* P = reinterpret_cast<double*>(base + rbytes + tbytes);
+  auto* scan = reinterpret_cast<ScanResult*>(base + rbytes + tbytes + pbytes);
+  pald_status st = scan_and_check(D, n, scan, o.validate != 0, s);
+  if (st != PALD_OK) return st;
+  if (o.flags & PALD_FLAG_IGNORE_TIES)
+    e = cudaMemsetAsync(tmap, 0, static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t), s);
+  else
+    e = launch_tie_map(D, n, tmap, s);
+  if (e == cudaSuccess) e = launch_cohesion_depth(D, U, R, n, C, tmap, scan, o.accum_mode, P, s);
+  if (e == cudaSuccess) e = launch_depth_merge(P, n, L, s);
+  return e == cudaSuccess ? PALD_OK : cuda_fail(e);
 }
 
 pald_status pald_validate(const float* D, int64_t n, pald_stream_t stream) {

@@ -44,7 +44,10 @@ pald_opts opts_or_default(const pald_opts* o);
 namespace {
 
 using FG = FocusS7;     // 64 x 64 tiles, 32-deep TMA stages
-using CG = CohesionS7;  // 64 x 64 tiles, 32-deep TMA stages
+// 64 x 64 tiles, 32-deep TMA stages, the scalar stage unrolled by 16 y (the
+// packed stage needs R in its paired column order, which the padded copies
+// of uneven order do not have)
+using CG = TileGeom<64, 1, 1, 1, 4, 32, 16>;
 static_assert(FG::B == 64 && CG::B == 64 && FG::H == 1 && CG::H == 1, "both passes share one tile list");
 constexpr int kB = 64;
 constexpr int kMaxGridY = 65535;  // matrices beyond it are strided over blockIdx.y

@@ -11,11 +11,18 @@ namespace pald {
 
 namespace {
 
+#ifndef PALD_COH_PACKED
+#define PALD_COH_PACKED 1
+#endif
+// The TMA pass-2 tile runs the packed stage (cohesion_stage_packed), which
+// reads R in the paired column order.
+constexpr bool kPackedTma = PALD_COH_PACKED != 0;
+
 __global__ void __launch_bounds__(256) reciprocal_kernel(const int32_t* __restrict__ U, float* __restrict__ R,
-                                                         int64_t n) {
+                                                         int64_t n, bool paired) {
   const bool vec = (n % 4) == 0 && (reinterpret_cast<uintptr_t>(U) % 16) == 0 &&
                    (reinterpret_cast<uintptr_t>(R) % 16) == 0;
-  for (int64_t row = blockIdx.x; row < n; row += gridDim.x) reciprocal_rows(U, n, R, n, row, vec);
+  for (int64_t row = blockIdx.x; row < n; row += gridDim.x) reciprocal_rows(U, n, R, n, row, vec, paired);
 }
 
 template <class Geo, int MODE, int MINB>
@@ -52,19 +59,23 @@ __device__ uint32_t g_cohesion_faults;
 #define PALD_COHESION_TMA_MINB 2
 #endif
 
-template <int MODE>
-__global__ void __launch_bounds__(CohesionS7::NT, PALD_COHESION_TMA_MINB)
+// With DEPTH the tiles also write their row sums to P (the fused local
+// depth, depth_partials).
+template <int MODE, bool DEPTH>
+__global__ void __launch_bounds__(CohesionTmaGeo<MODE>::NT, PALD_COHESION_TMA_MINB)
     cohesion_tma_kernel(const __grid_constant__ CUtensorMap tmD, const __grid_constant__ CUtensorMap tmR,
                         const float* __restrict__ D, int64_t n, float* __restrict__ C,
                         const uint32_t* __restrict__ tmap, const ScanResult* __restrict__ scan, int64_t T,
-                        int64_t t0) {
+                        int64_t t0, double* __restrict__ P) {
   extern __shared__ __align__(128) float smem_tma[];
   int bi, bj, slice;
   decode_tile(blockIdx.x + t0, T, 1, &bi, &bj, &slice);
-  TmaRing<4, CohesionS7::BK> ring;
+  using Geo = CohesionTmaGeo<MODE>;
+  TmaRing<4, Geo::BK> ring;
   uint32_t* tie_words = reinterpret_cast<uint32_t*>(ring.carve(smem_tma));
   const float S = focus_scale(scan->inv_min_pos_bits);
-  if (!cohesion_tile_tma<CohesionS7, MODE>(&tmD, &tmR, D, n, C, tmap, S, bi, bj, true, ring, tie_words) &&
+  if (!cohesion_tile_tma<Geo, MODE, DEPTH, kPackedTma>(&tmD, &tmR, D, n, C, tmap, S, bi, bj, true, ring,
+                                                              tie_words, false, P) &&
       threadIdx.x == 0)
     atomicOr(&g_cohesion_faults, 1u);
 }
@@ -95,10 +106,11 @@ bool tma_ok(const float* D, const float* R, const float* C, int64_t n) {
          reinterpret_cast<uintptr_t>(R) % 16 == 0 && reinterpret_cast<uintptr_t>(C) % 16 == 0;
 }
 
-template <int MODE>
+template <int MODE, bool DEPTH = false>
 cudaError_t launch_tma(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
-                       const ScanResult* scan, cudaStream_t s, int64_t t0 = 0, int64_t t1 = -1) {
-  using Geo = CohesionS7;
+                       const ScanResult* scan, cudaStream_t s, int64_t t0 = 0, int64_t t1 = -1,
+                       double* P = nullptr) {
+  using Geo = CohesionTmaGeo<MODE>;
   const int64_t T = (n + 63) / 64;
   if (t1 < 0) t1 = T * (T + 1) / 2;
   const int64_t ctas = t1 - t0;
@@ -109,9 +121,10 @@ cudaError_t launch_tma(const float* D, const float* R, int64_t n, float* C, cons
   if (e == cudaSuccess) e = encode_panel_map(&mR, R, n, n, Geo::BK);
   if (e != cudaSuccess) return e;
   const int smem = CohesionTmaSmem<Geo>::bytes(n);  // TMA ring + tie words
-  e = smem_opt_in(reinterpret_cast<const void*>(cohesion_tma_kernel<MODE>), CohesionTmaSmem<Geo>::MAX_BYTES);
+  e = smem_opt_in(reinterpret_cast<const void*>(cohesion_tma_kernel<MODE, DEPTH>), CohesionTmaSmem<Geo>::MAX_BYTES);
   if (e != cudaSuccess) return e;
-  cohesion_tma_kernel<MODE><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(mD, mR, D, n, C, tmap, scan, T, t0);
+  cohesion_tma_kernel<MODE, DEPTH><<<static_cast<unsigned>(ctas), Geo::NT, smem, s>>>(mD, mR, D, n, C, tmap, scan, T,
+                                                                                     t0, P);
   return cudaGetLastError();
 }
 
@@ -135,10 +148,10 @@ cudaError_t launch_mode(const float* D, const float* R, int64_t n, float* C, con
 
 }  // namespace
 
-cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_t s) {
+cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_t s, bool paired) {
   const int64_t cap = int64_t(sm_count()) * 16;
   const int64_t grid = n < cap ? n : cap;
-  reciprocal_kernel<<<static_cast<unsigned>(grid), 256, 0, s>>>(U, R, n);
+  reciprocal_kernel<<<static_cast<unsigned>(grid), 256, 0, s>>>(U, R, n, paired);
   return cudaGetLastError();
 }
 
@@ -182,10 +195,13 @@ cudaError_t encode_rect_map(CUtensorMap* map, const float* base, int64_t cols, i
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_cohesion_range(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
-                                  const ScanResult* scan, int accum_mode, int64_t t0, int64_t t1, cudaStream_t s) {
+cudaError_t launch_cohesion_range(const float* D, const int32_t* U, float* R, int64_t n, float* C,
+                                  const uint32_t* tmap, const ScanResult* scan, int accum_mode, int64_t t0, int64_t t1,
+                                  cudaStream_t s) {
   // the 64 x 64 tiles of the shard plan: TMA-staged when the layout allows
   const bool tma = tma_ok(D, R, C, n);
+  const cudaError_t e = launch_reciprocal(U, R, n, s, tma && kPackedTma);
+  if (e != cudaSuccess) return e;
   if (accum_mode == PALD_ACCUM_PLAIN)
     return tma ? launch_tma<PALD_ACCUM_PLAIN>(D, R, n, C, tmap, scan, s, t0, t1)
                : launch_t<CohesionS3, PALD_ACCUM_PLAIN, 1>(D, R, n, C, tmap, scan, s, t0, t1);
@@ -193,9 +209,24 @@ cudaError_t launch_cohesion_range(const float* D, const float* R, int64_t n, flo
              : launch_t<CohesionS3, PALD_ACCUM_COMPENSATED, 1>(D, R, n, C, tmap, scan, s, t0, t1);
 }
 
-cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+// R comes from the stream-ordered allocator (256-byte aligned).
+bool cohesion_depth_fused_ok(const float* D, const float* C, int64_t n) { return tma_ok(D, D, C, n); }
+
+cudaError_t launch_cohesion_depth(const float* D, const int32_t* U, float* R, int64_t n, float* C,
+                                  const uint32_t* tmap, const ScanResult* scan, int accum_mode, double* P,
+                                  cudaStream_t s) {
+  if (!tma_ok(D, R, C, n)) return cudaErrorInvalidValue;
+  const cudaError_t e = launch_reciprocal(U, R, n, s, kPackedTma);
+  if (e != cudaSuccess) return e;
+  if (accum_mode == PALD_ACCUM_PLAIN) return launch_tma<PALD_ACCUM_PLAIN, true>(D, R, n, C, tmap, scan, s, 0, -1, P);
+  return launch_tma<PALD_ACCUM_COMPENSATED, true>(D, R, n, C, tmap, scan, s, 0, -1, P);
+}
+
+cudaError_t launch_cohesion(const float* D, const int32_t* U, float* R, int64_t n, float* C, const uint32_t* tmap,
                             const ScanResult* scan, int accum_mode, int schedule, cudaStream_t s) {
   if (schedule < 0) schedule = default_cohesion_schedule(n);
+  const cudaError_t e = launch_reciprocal(U, R, n, s, schedule == 7 && tma_ok(D, R, C, n) && kPackedTma);
+  if (e != cudaSuccess) return e;
   if (accum_mode == PALD_ACCUM_PLAIN) return launch_mode<PALD_ACCUM_PLAIN>(D, R, n, C, tmap, scan, schedule, s);
   return launch_mode<PALD_ACCUM_COMPENSATED>(D, R, n, C, tmap, scan, schedule, s);
 }

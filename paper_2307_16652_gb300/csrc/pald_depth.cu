@@ -49,6 +49,18 @@ __global__ void __launch_bounds__(kDepthThreads) local_depth_kernel(const float*
   }
 }
 
+// The fused local depth's last step: L[x] = the sum over column blocks b
+// (in order) of P[b * n + x], rounded once to FP32.  One thread per row;
+// the threads of a warp read consecutive rows of one block.
+__global__ void __launch_bounds__(kDepthThreads) depth_merge_kernel(const double* __restrict__ P, int64_t n,
+                                                                   int64_t nb, float* __restrict__ L) {
+  const int64_t x = static_cast<int64_t>(blockIdx.x) * kDepthThreads + threadIdx.x;
+  if (x >= n) return;
+  double s = 0.0;
+  for (int64_t b = 0; b < nb; ++b) s += __ldg(P + b * n + x);
+  L[x] = static_cast<float>(s);
+}
+
 __global__ void __launch_bounds__(256) strong_ties_kernel(const float* __restrict__ C, int64_t elems,
                                                           float threshold, uint8_t* __restrict__ T) {
   for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < elems;
@@ -57,6 +69,13 @@ __global__ void __launch_bounds__(256) strong_ties_kernel(const float* __restric
 }
 
 }  // namespace
+
+cudaError_t launch_depth_merge(const double* P, int64_t n, float* L, cudaStream_t s) {
+  const int64_t nb = (n + 63) / 64;
+  depth_merge_kernel<<<static_cast<unsigned>((n + kDepthThreads - 1) / kDepthThreads), kDepthThreads, 0, s>>>(P, n, nb,
+                                                                                                           L);
+  return cudaGetLastError();
+}
 
 }  // namespace pald
 

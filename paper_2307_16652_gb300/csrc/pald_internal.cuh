@@ -205,19 +205,33 @@ cudaError_t smem_opt_in(const void* fn, int bytes);
 cudaError_t launch_scan(const float* D, int64_t n, ScanResult* out, bool validate, cudaStream_t s);
 cudaError_t launch_focus(const float* D, int64_t n, int32_t* U, const ScanResult* scan, int schedule,
                          cudaStream_t s);
-cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_t s);
+// R = 1/u with a zero diagonal; `paired`: the column order of the packed
+// pass-2 stage (reciprocal_rows).
+cudaError_t launch_reciprocal(const int32_t* U, float* R, int64_t n, cudaStream_t s, bool paired = false);
 // The 64 x 64 super-tiles [t0, t1) of a pass, in the launch order of
 // decode_tile (the units of a shard plan); TMA-staged when the layout allows.
 cudaError_t launch_focus_range(const float* D, int64_t n, int32_t* U, const ScanResult* scan, int64_t t0, int64_t t1,
                                cudaStream_t s);
-cudaError_t launch_cohesion_range(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
-                                  const ScanResult* scan, int accum_mode, int64_t t0, int64_t t1, cudaStream_t s);
+cudaError_t launch_cohesion_range(const float* D, const int32_t* U, float* R, int64_t n, float* C,
+                                  const uint32_t* tmap, const ScanResult* scan, int accum_mode, int64_t t0, int64_t t1,
+                                  cudaStream_t s);
 // Clears and fills the tie map (tie_map_words(n) words at `map`).
 cudaError_t launch_tie_map(const float* D, int64_t n, uint32_t* map, cudaStream_t s);
+// Pass 2: first R = 1/u from U into the scratch R (n x n FP32, in the
+// layout the chosen kernel reads), then the tiles.
 // `tmap` null: every stage takes the long loop (same result, slower).
 // `scan` is the matrix's scan summary (launch_scan), for the pass-1 scale.
-cudaError_t launch_cohesion(const float* D, const float* R, int64_t n, float* C, const uint32_t* tmap,
+cudaError_t launch_cohesion(const float* D, const int32_t* U, float* R, int64_t n, float* C, const uint32_t* tmap,
                             const ScanResult* scan, int accum_mode, int schedule, cudaStream_t s);
+// Pass 2 on the TMA tiles (all of them) with the fused local depth: the
+// tiles also write their row sums to P ([ceil(n/64)][n] FP64, every entry
+// written once), which launch_depth_merge then adds up in order.  Needs the
+// TMA layout (cohesion_depth_fused_ok; R 16-byte aligned).
+bool cohesion_depth_fused_ok(const float* D, const float* C, int64_t n);
+cudaError_t launch_cohesion_depth(const float* D, const int32_t* U, float* R, int64_t n, float* C,
+                                  const uint32_t* tmap, const ScanResult* scan, int accum_mode, double* P,
+                                  cudaStream_t s);
+cudaError_t launch_depth_merge(const double* P, int64_t n, float* L, cudaStream_t s);
 // Read and clear the device fault words of the pass-1, pass-2 and batched
 // kernels (nonzero: a bounded wait gave up).  Synchronise `s`.
 cudaError_t take_cohesion_faults(uint32_t* out, cudaStream_t s);

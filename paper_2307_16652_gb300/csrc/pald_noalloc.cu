@@ -83,12 +83,12 @@ extern "C" pald_status pald_cohesion_noalloc(const float* D, const int32_t* U, i
     if (e != cudaSuccess) return cuda_fail(e);
     if ((st = status_from_scan(host)) != PALD_OK) return st;
   }
-  // R is written in full (every entry of the n x n block) before it is read,
-  // so nothing left by an earlier call leaks into this one.
-  e = launch_reciprocal(U, R, n, s);
-  // No tie map (it would need scratch): every stage takes the long form,
-  // which gives the same bits as pald_cohesion's mix of forms.
-  if (e == cudaSuccess) e = launch_cohesion(D, R, n, C, nullptr, scan, o.accum_mode, o.schedule_id, s);
+  // R is written in full (every entry of the n x n block, inside
+  // launch_cohesion) before it is read, so nothing left by an earlier call
+  // leaks into this one.  No tie map (it would need scratch): every stage
+  // takes the long form, which gives the same bits as pald_cohesion's mix of
+  // forms.
+  e = launch_cohesion(D, U, R, n, C, nullptr, scan, o.accum_mode, o.schedule_id, s);
   if (e != cudaSuccess) return cuda_fail(e);
   return PALD_OK;
 }

@@ -152,8 +152,7 @@ pald_status pald_cohesion_tiles(const float* D, const int32_t* U, int64_t n, int
     e = cudaMemsetAsync(tmap, 0, static_cast<size_t>(tie_map_words(n)) * sizeof(uint32_t), s);
   else
     e = launch_tie_map(D, n, tmap, s);
-  if (e == cudaSuccess) e = launch_reciprocal(U, R, n, s);
-  if (e == cudaSuccess) e = launch_cohesion_range(D, R, n, C, tmap, scan, o.accum_mode, t0, t1, s);
+  if (e == cudaSuccess) e = launch_cohesion_range(D, U, R, n, C, tmap, scan, o.accum_mode, t0, t1, s);
   if (e != cudaSuccess) return cuda_fail(e);
   return PALD_OK;
 }

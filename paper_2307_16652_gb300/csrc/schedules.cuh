@@ -5,6 +5,8 @@
 // paper_2307_16652_gb300/autotune.py); pald_opts.schedule_id overrides them.
 #pragma once
 
+#include <type_traits>
+
 #include "tile_geom.cuh"
 
 namespace pald {
@@ -28,7 +30,18 @@ using CohesionS3 = TileGeom<64, 1, 1, 1, 4, 32>;  // deeper stages
 using CohesionS4 = TileGeom<64, 2, 1, 1, 2, 32>;  // 4x2 pairs/thread, deeper stages
 using CohesionS5 = TileGeom<64, 1, 1, 1, 4, 32, kMergeEvery>;  // 32-deep, loop unrolled by one merge chunk
 using CohesionS6 = TileGeom<64, 1, 1, 1, 4, 64, (kMergeEvery > 8 ? kMergeEvery : 8)>;  // 64-deep stages, unrolled by 8
-using CohesionS7 = TileGeom<64, 1, 1, 1, 4, 32, 16>;  // S3's tile, TMA-staged, two CTAs per SM
+// S3's tile, TMA-staged, two CTAs per SM, packed stage (cohesion_stage_packed).
+// Measured at n = 8192 / 16384 on GB300: a whole stage unrolled (32 y) 47.98
+// / 375.3 ms, 16 y 49.37 / 386.5, 8 y 56.8 / 445.5; the scalar stage with 16 y
+// 49.70 / 389.0.
+// PALD_ACCUM_PLAIN keeps 16 y: unrolled by 32 its build spills 640 bytes.
+#ifndef PALD_COH_UNR
+#define PALD_COH_UNR 32
+#endif
+using CohesionS7 = TileGeom<64, 1, 1, 1, 4, 32, PALD_COH_UNR>;
+using CohesionS7Plain = TileGeom<64, 1, 1, 1, 4, 32, 16>;
+template <int MODE>
+using CohesionTmaGeo = std::conditional_t<MODE == PALD_ACCUM_PLAIN, CohesionS7Plain, CohesionS7>;
 
 inline int sm_count() {
   int dev = 0, sms = 148;

@@ -63,6 +63,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
     assert lib.pald_tie_map(None, 8, fake, None) == INVALID
     assert lib.pald_tie_map(fake, 1, fake, None) == INVALID
     assert lib.pald_local_depth(None, 8, fake, None) == INVALID
+    assert lib.pald_cohesion_depth(fake, fake, 8, fake, None, ctypes.byref(o), None) == INVALID  # null L
+    assert lib.pald_cohesion_depth(fake, fake, 1, fake, fake, ctypes.byref(o), None) == INVALID
     assert lib.pald_local_depth(fake, 1, fake, None) == INVALID
     assert lib.pald_strong_ties(fake, 8, float("nan"), fake, None) == INVALID
     assert lib.pald_strong_ties(fake, 8, 0.5, None, None) == INVALID
