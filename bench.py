@@ -183,6 +183,49 @@ def csrc_digest() -> str:
     return h.hexdigest()[:16]
 
 
+# The capture the traffic record comes from: one launch of each pass kernel
+# at n = 8192 (inputs larger than L2, a few GB on the device), DRAM counters
+# only (a single-pass capture), after the same bench command exited 0.
+TRAFFIC_N = 8192
+TRAFFIC_CAPTURE = ("ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                   "--clock-control none -k regex:'focus_tma_kernel|cohesion_tma_kernel' -s 6 -c 2 --csv "
+                   "--log-file traffic8192.csv python bench.py --workload paper-8192 --steps 1 --warmup 3 "
+                   "--no-e2e --no-cpu-baseline --no-batched --no-extras")
+UNITS = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-9, "us": 1e-6, "ms": 1e-3,
+         "nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3}
+
+
+def write_traffic_record(csv_path: str, out_path: str):
+    """profiles/traffic.json from the CSV of TRAFFIC_CAPTURE, stamped with the
+    digest of the sources it ran on (run this beside the capture)."""
+    import collections
+    import csv
+
+    with open(csv_path) as f:
+        rows = list(csv.reader(f))
+    hdr = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hdr]
+    ki, mi, vi, ui = (h.index(c) for c in ("Kernel Name", "Metric Name", "Metric Value", "Metric Unit"))
+    per = collections.defaultdict(dict)
+    for r in rows[hdr + 1:]:
+        if len(r) <= vi:
+            continue
+        name = next((k for k in ("focus_tma_kernel", "cohesion_tma_kernel") if k in r[ki]), None)
+        if name:
+            per[name][r[mi]] = float(r[vi].replace(",", "")) * UNITS.get(r[ui], 1)
+    rec = {"csrc_digest": csrc_digest(), "source": TRAFFIC_CAPTURE,
+           "scaling": "dram bytes per launch at n, scaled to other n by unique triplets C(n,3)",
+           "digest_of": "bench.TRAFFIC_SOURCES at the time of the capture", "kernels": {}}
+    for k, m in sorted(per.items()):
+        rd, wr = m["dram__bytes_read.sum"], m["dram__bytes_write.sum"]
+        rec["kernels"][k] = {"n": TRAFFIC_N, "dram_bytes": int(rd + wr), "read": int(rd), "write": int(wr),
+                             "ms_under_ncu": round(m["gpu__time_duration.sum"] * 1e3, 3)}
+    with open(out_path, "w") as f:
+        json.dump(rec, f, indent=1)
+        f.write("\n")
+    return rec
+
+
 def traffic_for(kernel: str, n: int):
     """DRAM bytes per launch from the committed ncu summary, scaled to n by
     the units processed; None when absent or taken on different kernel code."""
@@ -513,7 +556,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the other single-matrix workloads")
     ap.add_argument("--batched-count", type=int, default=2000)
     ap.add_argument("--oracle-rows", type=int, default=0)
+    ap.add_argument("--traffic-from", metavar="CSV",
+                    help="write the traffic record from the CSV of TRAFFIC_CAPTURE and exit (no GPU work)")
+    ap.add_argument("--traffic-out", default=os.path.join(ROOT, "profiles", "traffic.json"))
     args = ap.parse_args()
+    if args.traffic_from:
+        print(json.dumps(write_traffic_record(args.traffic_from, args.traffic_out), indent=1))
+        return
     if args.warmup < 3:
         raise SystemExit("at least 3 warm-up steps are required")
     rank, world, local = dist_setup(args)
