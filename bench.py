@@ -383,9 +383,10 @@ def run_ours(args, rank, world, local):
 
 def run_other_workloads(props, sm_max):
     """Per-pass rates on the other single-matrix configs: tie-heavy-4096 (a
-    tie in nearly every 32-y stage: pass 2 runs its 8-slot long form
-    throughout) and precision-16384, plus the pairwise strip variant on the
-    paper recipe at n = 8192 (u never stored)."""
+    tie in nearly every 8-y group: pass 2 runs its 8-slot long form
+    throughout) and precision-16384; on the paper recipe at n = 8192, pass 2
+    with the fused local depth and the pairwise strip variant (u never
+    stored)."""
     import torch
 
     import paper_2307_16652_gb300 as pald

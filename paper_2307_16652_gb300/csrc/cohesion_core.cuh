@@ -38,9 +38,9 @@
 // in row x or z (a marked tie, so not here), or y == z or y == x with
 // b == 0, where x == z and both r vanish (r_xx = 0) or the points are
 // duplicates (a marked tie again).  So every add that differs from the long
-// form adds +0, and both forms give the same bits.  Which stages may use the
+// form adds +0, and both forms give the same bits.  Which y may use the
 // short form comes from the tie map (one bit per 64 x 64 block pair and
-// 32 y; tie_map_core.cuh builds it).
+// 8 y; tie_map_core.cuh builds it).
 //
 // Accumulation (PALD_ACCUM_COMPENSATED): the pair {S_xz, S_zx} is an FP32
 // partial over kMergeEvery = 8 consecutive y (fold_phase below places the
@@ -57,6 +57,8 @@
 // mul_pair below).  PALD_ACCUM_PLAIN keeps one FP32 running sum (the
 // precision baseline), normalised the same way.
 #pragma once
+
+#include <type_traits>
 
 #include "focus_core.cuh"
 
@@ -176,18 +178,20 @@ __device__ __forceinline__ void unpack2(uint64_t v, float& lo, float& hi) {
 }
 
 // One pipeline stage (BK consecutive y) of a CTA tile, long or short form,
-// in chunks of Geo::UNR y: the first `kend` y of the stage (a multiple of
-// UNR; the zero-filled y past n add +0, so whole chunks of them are skipped).
-template <class Geo, int MODE, bool SHORT>
+// in chunks of U y: y kbeg .. kend-1 of the stage (multiples of U; the
+// zero-filled y past n add +0, so whole chunks of them are skipped).
+template <class Geo, int MODE, bool SHORT, int U = Geo::UNR>
 __device__ __forceinline__ void cohesion_stage(const float* ad, const float* ar, const float* bd, const float* br,
                                                int tx, int tz, float S, const float (&cv)[Geo::TX][Geo::TY],
                                                uint64_t (&sacc)[Geo::TX][Geo::TY],
-                                               uint64_t (&hacc)[Geo::TX][Geo::TY], int kend = Geo::BK) {
+                                               uint64_t (&hacc)[Geo::TX][Geo::TY], int kend = Geo::BK,
+                                               int kbeg = 0) {
   constexpr int TX = Geo::TX, TY = Geo::TY;
+  static_assert(U % kMergeEvery == 0, "chunks hold whole merge chunks");
 #pragma unroll 1
-  for (int k0 = 0; k0 < kend; k0 += Geo::UNR) {
+  for (int k0 = kbeg; k0 < kend; k0 += U) {
 #pragma unroll
-    for (int k = 0; k < Geo::UNR; ++k) {
+    for (int k = 0; k < U; ++k) {
       const int kk = k0 + k;
       float a1[TX], r1[TX], a2[TY], r2[TY];
 #pragma unroll
@@ -266,19 +270,20 @@ __device__ __forceinline__ void cohesion_step2_long(uint64_t& sx, uint64_t& sz, 
   sz = L == 0 ? pack2(pz, z1) : pack2(z0, pz);
 }
 
-template <class Geo, int MODE, bool SHORT>
+template <class Geo, int MODE, bool SHORT, int U = Geo::UNR>
 __device__ __forceinline__ void cohesion_stage_packed(const float* ad, const float* ar, const float* bd,
                                                       const float* br, int tx, int tz, float S,
                                                       const float (&cv)[4][4], uint64_t (&sx)[4][2],
                                                       uint64_t (&sz)[4][2], uint64_t (&hx)[4][2],
-                                                      uint64_t (&hz)[4][2], int kend) {
+                                                      uint64_t (&hz)[4][2], int kend, int kbeg = 0) {
   static_assert(Geo::TX == 4 && Geo::TY == 4 && Geo::GX == 1 && Geo::GY == 1 && Geo::BX == 64 && Geo::BY == 64,
                 "the packed stage is for 64 x 64 tiles with 4 x 4 pairs per thread");
+  static_assert(U % kMergeEvery == 0, "chunks hold whole merge chunks");
   constexpr int kSlot[4] = {0, 2, 1, 3};  // register of r_xy(i) in the paired order
 #pragma unroll 1
-  for (int k0 = 0; k0 < kend; k0 += Geo::UNR) {
+  for (int k0 = kbeg; k0 < kend; k0 += U) {
 #pragma unroll
-    for (int k = 0; k < Geo::UNR; ++k) {
+    for (int k = 0; k < U; ++k) {
       const int kk = k0 + k;
       float a1[4], rx[4], a2[4];
       lds<4>(ad + kk * 64 + 4 * tx, a1);
@@ -353,11 +358,10 @@ struct TieCursor {
                __ldg(tmap + dm.nb * dm.nb * dm.wpp + bz) != 0u;
   }
   __device__ __forceinline__ uint32_t tied(int64_t st) const {
-    constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
     if (all_long) return 1u;
     if (st >= nstages) return 0u;
     const int64_t g = (st * BK) / kTieGroup;
-    return (__ldg(row + (g >> 5)) >> (g & 31)) & kGroupMask;
+    return (__ldg(row + (g >> 5)) >> (g & 31)) & tie_stage_mask<BK>();
   }
 };
 
@@ -532,7 +536,7 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
 // in the loop, and the kernel fits two CTAs per SM (four warps per
 // scheduler).
 
-constexpr int kTieWordsMax = 1024;  // tie-map words of one block pair for n <= 2^20
+constexpr int kTieWordsMax = ((1 << 20) / kTieGroup + 31) / 32;  // tie-map words of one block pair for n <= 2^20
 
 template <class Geo>
 struct CohesionTmaSmem {
@@ -638,7 +642,25 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
       }
   }
 
-  constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
+  // y [kb, ke) of the stage in buffer buf, in one form, in chunks of U y
+  auto run = [&](auto short_form, auto unroll, int buf, int kb, int ke) {
+    constexpr bool SHORT = decltype(short_form)::value;
+    constexpr int U = decltype(unroll)::value;
+    if constexpr (PACKED)
+      cohesion_stage_packed<Geo, MODE, SHORT, U>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
+                                                 ring.panel(buf, 3), tx, tz, S, cv, sx, sz, hx, hz, ke, kb);
+    else
+      cohesion_stage<Geo, MODE, SHORT, U>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
+                                          ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, ke, kb);
+  };
+  using Short = std::true_type;
+  using Long = std::false_type;
+  // a stage with some of its tie groups marked runs chunks of CH y, each in
+  // the form its groups need (CH: whole groups and whole merge chunks)
+  constexpr int CH = kTieGroup > kMergeEvery ? kTieGroup : kMergeEvery;
+  constexpr int GPC = CH / kTieGroup;
+  constexpr uint32_t kStageMask = tie_stage_mask<BK>();
+  static_assert(BK % CH == 0, "a stage holds whole chunks");
   const CUtensorMap* const maps[4] = {tmD, tmR, tmD, tmR};
   const int cols[4] = {bi * 64, bi * 64, bj * 64, bj * 64};
   const bool ok = tma_pipeline(
@@ -646,22 +668,20 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
       [&](int st, int buf) {
         if (!active) return;
         const int g = st * BK / kTieGroup;
-        const int kend = stage_extent<BK, Geo::UNR>(n, st);
-        const bool tied = (tie_words[g >> 5] >> (g & 31)) & kGroupMask;
-        if constexpr (PACKED) {
-          if (tied)
-            cohesion_stage_packed<Geo, MODE, false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
-                                                    ring.panel(buf, 3), tx, tz, S, cv, sx, sz, hx, hz, kend);
-          else
-            cohesion_stage_packed<Geo, MODE, true>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
-                                                   ring.panel(buf, 3), tx, tz, S, cv, sx, sz, hx, hz, kend);
+        const uint32_t bits = (tie_words[g >> 5] >> (g & 31)) & kStageMask;
+        if (bits == 0u) {
+          run(Short(), std::integral_constant<int, Geo::UNR>(), buf, 0, stage_extent<BK, Geo::UNR>(n, st));
+        } else if (bits == kStageMask) {
+          run(Long(), std::integral_constant<int, Geo::UNR>(), buf, 0, stage_extent<BK, Geo::UNR>(n, st));
         } else {
-          if (tied)
-            cohesion_stage<Geo, MODE, false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
-                                             ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, kend);
-          else
-            cohesion_stage<Geo, MODE, true>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2),
-                                            ring.panel(buf, 3), tx, tz, S, cv, sacc, hacc, kend);
+          const int ke = stage_extent<BK, CH>(n, st);
+#pragma unroll 1
+          for (int c = 0; c * CH < ke; ++c) {
+            if ((bits >> (c * GPC)) & ((1u << GPC) - 1u))
+              run(Long(), std::integral_constant<int, CH>(), buf, c * CH, c * CH + CH);
+            else
+              run(Short(), std::integral_constant<int, CH>(), buf, c * CH, c * CH + CH);
+          }
         }
       });
   __syncthreads();
@@ -693,8 +713,8 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
 // y are one 16-byte vector).  Only the ten pairs i <= j are formed (pair
 // (j, i) repeats pair (i, j) with the two lanes swapped).  Each lane repeats
 // the tile's operations on its pair in the same order: the same step in the
-// form the tile's stage takes (the tie map's bit of block pair (x0 / 64,
-// x0 / 64) per 32 y), the fold after the same y, the same final merge.  The
+// form the tile takes (the tie map's bit of block pair (x0 / 64, x0 / 64)
+// per group of 8 y), the fold after the same y, the same final merge.  The
 // tile also runs zero-filled y past n; those add +0, and folding the last
 // partial into H leaves H + S, and so the merged value, unchanged: stopping
 // at the first multiple of 4 past n gives the same bits.

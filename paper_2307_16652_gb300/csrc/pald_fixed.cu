@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(FX::NT, 1)
       Ax[i][j] = 0;
       Az[i][j] = 0;
     }
-  constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
+  constexpr uint32_t kGroupMask = tie_stage_mask<BK>();  // any group of the stage marked
   const CUtensorMap* const maps[6] = {&tmD, &tmH, &tmL, &tmD, &tmH, &tmL};
   const int cols[6] = {bi * 64, bi * 64, bi * 64, bj * 64, bj * 64, bj * 64};
   const bool ok = tma_pipeline(

@@ -168,18 +168,29 @@ __host__ __device__ __forceinline__ void tri_decode(int64_t t, int64_t T, int* b
 // Pass 2 has a 4-instruction form that is exact unless a one-sided tie
 // d_xy == d_xz (or d_zy == d_zx) occurs; such a tie is two equal entries in
 // one row of D.  The map holds one bit per (pair of 64-blocks {X, Z}, group
-// of 32 consecutive y): set when some row r of X or Z has two equal entries
+// of 8 consecutive y): set when some row r of X or Z has two equal entries
 // at columns p and q with the block of q being the other side of the pair
 // and p in the y group.  `dirty[b]` marks a block with a row whose repeats
 // were too many to list; every stage of a tile touching it takes the exact
-// loop.  Layout: words[nb][nb][wpp] then dirty[nb], all uint32.
+// loop.  Layout: words[nb][nb][wpp] then dirty[nb], all uint32.  (Groups of
+// 8 y rather than a whole 32-y stage: a sparse tie marks a quarter of the
+// long-form work, and a stage with some marked groups runs the long form
+// on those groups only.)
 constexpr int kTieBlock = 64;  // rows / columns per block of the map
-constexpr int kTieGroup = 32;  // y per group of the map
+constexpr int kTieGroup = 8;   // y per group of the map
 
 struct TieMapDims {
   int64_t nb;   // blocks per side, ceil(n / 64)
-  int64_t wpp;  // words per block pair, ceil(ceil(n / 32) / 32)
+  int64_t wpp;  // words per block pair, ceil(ceil(n / 8) / 32)
 };
+
+// The bits of one stage of BK y in its word of the map (they never straddle
+// two words): nonzero means some group of the stage needs the long form.
+template <int BK>
+__host__ __device__ constexpr uint32_t tie_stage_mask() {
+  static_assert(BK % kTieGroup == 0 && 32 % (BK / kTieGroup) == 0, "a stage holds whole groups of one word");
+  return BK / kTieGroup == 32 ? ~0u : (1u << (BK / kTieGroup)) - 1u;
+}
 
 __host__ __device__ __forceinline__ TieMapDims tie_map_dims(int64_t n) {
   TieMapDims d;

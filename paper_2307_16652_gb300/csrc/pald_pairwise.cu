@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(PG::NT, 2)
       hacc[i][jj] = pack2(kMergeBias, kMergeBias);
     }
   }
-  constexpr uint32_t kGroupMask = BK == 64 ? 3u : 1u;
+  constexpr uint32_t kGroupMask = tie_stage_mask<BK>();  // any group of the stage marked
   const CUtensorMap* const maps[3] = {&tmD, &tmR, &tmD};
   const int cols[3] = {bx * 64, static_cast<int>(X0 - x0), bz * 64};
   const bool ok = tma_pipeline(

@@ -71,14 +71,16 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
 
 
 def test_tie_map_size():
-    # nb = ceil(n/64) blocks, wpp = ceil(ceil(n/32)/32) words per block pair, plus nb dirty words
+    # nb = ceil(n/64) blocks, wpp = ceil(ceil(n/8)/32) words per block pair, plus nb dirty words
     assert binding.pald_tie_map_words(1) == 0
     assert binding.pald_tie_map_words(2) == 1 * 1 * 1 + 1
     assert binding.pald_tie_map_words(64) == 1 + 1
     assert binding.pald_tie_map_words(65) == 2 * 2 * 1 + 2
-    assert binding.pald_tie_map_words(1024) == 16 * 16 * 1 + 16
-    assert binding.pald_tie_map_words(1025) == 17 * 17 * 2 + 17
-    assert binding.pald_tie_map_words(65536) == 1024 * 1024 * 64 + 1024
+    assert binding.pald_tie_map_words(256) == 4 * 4 * 1 + 4
+    assert binding.pald_tie_map_words(257) == 5 * 5 * 2 + 5
+    assert binding.pald_tie_map_words(1024) == 16 * 16 * 4 + 16
+    assert binding.pald_tie_map_words(1025) == 17 * 17 * 5 + 17
+    assert binding.pald_tie_map_words(65536) == 1024 * 1024 * 256 + 1024
 
 
 def test_batched_argument_checks(lib):

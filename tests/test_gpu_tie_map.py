@@ -32,7 +32,7 @@ def expected_map(D: np.ndarray):
     """Host restatement of the map (rows of at most one hash pass, n <= 8192)."""
     n = D.shape[0]
     nb = -(-n // 64)
-    wpp = -(-(-(-n // 32)) // 32)
+    wpp = -(-(-(-n // 8)) // 32)  # groups of 8 y, 32 groups per word
     words = np.zeros(nb * nb * wpp, dtype=np.uint32)
     dirty = np.zeros(nb, dtype=np.uint32)
     bits = (D + np.float32(0.0)).view(np.uint32)
@@ -48,7 +48,7 @@ def expected_map(D: np.ndarray):
             p, q = p[keep], q[keep]
             a = np.minimum(r // 64, q // 64)
             b = np.maximum(r // 64, q // 64)
-            grp = p // 32
+            grp = p // 8
             idx = (a * nb + b) * wpp + grp // 32
             np.bitwise_or.at(words, idx, (np.uint32(1) << (grp % 32).astype(np.uint32)))
     return words, dirty
