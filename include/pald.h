@@ -324,17 +324,18 @@ pald_status pald_strong_ties(const float* C, int64_t n, float threshold, uint8_t
 
 /*
  * pald_tie_map - diagnostic: the tie map that pald_cohesion builds for D and
- * reads to pick, per tile and group of 8 y, between its short inner loop
+ * reads to pick, per tile and group of y, between its short inner loop
  * (valid when no one-sided tie d_xy == d_xz or d_zy == d_zx can occur) and
  * its long one.  The paper has no counterpart; both loops compute Sec. 2
  * eq. (fxz) with the Sec. 5 tie split and give identical bits.
  *   D    device, n x n FP32 (the input contract above).
  *   map  device uint32 array of pald_tie_map_words(n) words, overwritten.
- *        With nb = ceil(n/64) and wpp = ceil(ceil(n/8)/32): word
+ *        With groups of G = 8 y for n <= 65536 and G = 32 y beyond,
+ *        nb = ceil(n/64) and wpp = ceil(ceil(n/G)/32): word
  *        (a*nb + b)*wpp + g/32, a <= b, holds bit g%32 set when some row r
  *        in block a or b (rows 64a.., 64b..) has equal entries at two
  *        columns p != q with q in the other block of the pair and p in
- *        y group g (columns 8g..8g+7); words nb*nb*wpp + a (a < nb) are
+ *        y group g (columns G*g .. G*g+G-1); words nb*nb*wpp + a (a < nb) are
  *        nonzero when a row of block a had too many repeated values to list
  *        (the tile then runs the long loop throughout).
  * Errors: INVALID_ARG (null pointer, n out of range); CUDA.

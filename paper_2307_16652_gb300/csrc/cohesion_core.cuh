@@ -348,9 +348,11 @@ template <int BK>
 struct TieCursor {
   const uint32_t* row;
   int64_t nstages;
+  int group;
   bool all_long;
   __device__ __forceinline__ TieCursor(const uint32_t* tmap, int64_t n, int64_t X0, int64_t Z0) {
     const TieMapDims dm = tie_map_dims(n);
+    group = dm.group;
     const int64_t bx = X0 / kTieBlock, bz = Z0 / kTieBlock;
     row = tmap + (bx * dm.nb + bz) * dm.wpp;
     nstages = (n + BK - 1) / BK;
@@ -360,8 +362,8 @@ struct TieCursor {
   __device__ __forceinline__ uint32_t tied(int64_t st) const {
     if (all_long) return 1u;
     if (st >= nstages) return 0u;
-    const int64_t g = (st * BK) / kTieGroup;
-    return (__ldg(row + (g >> 5)) >> (g & 31)) & tie_stage_mask<BK>();
+    const TieStage ts = tie_stage(st, BK, group);
+    return (__ldg(row + (ts.g >> 5)) >> (ts.g & 31)) & ts.mask;
   }
 };
 
@@ -536,7 +538,9 @@ __device__ __forceinline__ void cohesion_tile(const float* __restrict__ D, const
 // in the loop, and the kernel fits two CTAs per SM (four warps per
 // scheduler).
 
-constexpr int kTieWordsMax = ((1 << 20) / kTieGroup + 31) / 32;  // tie-map words of one block pair for n <= 2^20
+// tie-map words of one block pair for any n <= 2^20
+constexpr int kTieWordsMax = ((1 << 20) / kTieGroupCoarse + 31) / 32;
+static_assert((kTieFineMaxN / kTieGroupFine + 31) / 32 <= kTieWordsMax, "fine maps fit too");
 
 template <class Geo>
 struct CohesionTmaSmem {
@@ -618,6 +622,7 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
 
   if (threadIdx.x == 0) ring.init();
   // the tile's tie-map row (all ones when there is no map or a block is dirty)
+  const int group = tie_map_dims(n).group;
   {
     const TieMapDims dm = tie_map_dims(n);
     const int64_t bx = bi, bz = bj;  // 64-wide tiles are the map's blocks
@@ -656,28 +661,29 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
   using Short = std::true_type;
   using Long = std::false_type;
   // a stage with some of its tie groups marked runs chunks of CH y, each in
-  // the form its groups need (CH: whole groups and whole merge chunks)
-  constexpr int CH = kTieGroup > kMergeEvery ? kTieGroup : kMergeEvery;
-  constexpr int GPC = CH / kTieGroup;
-  constexpr uint32_t kStageMask = tie_stage_mask<BK>();
-  static_assert(BK % CH == 0, "a stage holds whole chunks");
+  // the form its groups need (CH: whole fine groups and whole merge chunks;
+  // coarse groups cover a stage, so their stages are never mixed)
+  constexpr int CH = kTieGroupFine > kMergeEvery ? kTieGroupFine : kMergeEvery;
+  static_assert(BK % CH == 0 && CH % kTieGroupFine == 0, "a stage holds whole chunks");
   const CUtensorMap* const maps[4] = {tmD, tmR, tmD, tmR};
   const int cols[4] = {bi * 64, bi * 64, bj * 64, bj * 64};
   const bool ok = tma_pipeline(
       ring, nstages, [&](int q) { ring.issue(q, maps, cols); },
       [&](int st, int buf) {
         if (!active) return;
-        const int g = st * BK / kTieGroup;
-        const uint32_t bits = (tie_words[g >> 5] >> (g & 31)) & kStageMask;
+        const TieStage ts = tie_stage(st, BK, group);
+        const uint32_t bits = (tie_words[ts.g >> 5] >> (ts.g & 31)) & ts.mask;
         if (bits == 0u) {
           run(Short(), std::integral_constant<int, Geo::UNR>(), buf, 0, stage_extent<BK, Geo::UNR>(n, st));
-        } else if (bits == kStageMask) {
+        } else if (bits == ts.mask) {
           run(Long(), std::integral_constant<int, Geo::UNR>(), buf, 0, stage_extent<BK, Geo::UNR>(n, st));
-        } else {
+        } else {  // fine groups only
           const int ke = stage_extent<BK, CH>(n, st);
+          const int gpc = CH / group;  // groups per chunk
+          const uint32_t cmask = (1u << gpc) - 1u;
 #pragma unroll 1
           for (int c = 0; c * CH < ke; ++c) {
-            if ((bits >> (c * GPC)) & ((1u << GPC) - 1u))
+            if ((bits >> (c * gpc)) & cmask)
               run(Long(), std::integral_constant<int, CH>(), buf, c * CH, c * CH + CH);
             else
               run(Short(), std::integral_constant<int, CH>(), buf, c * CH, c * CH + CH);
@@ -788,7 +794,7 @@ __device__ __forceinline__ void cohesion_group(const float* __restrict__ Dp, con
   const int64_t bx = x0 / kTieBlock;
   const bool all_long = tmap == nullptr || __ldg(tmap + dm.nb * dm.nb * dm.wpp + bx) != 0u;
   const uint32_t* trow = tmap + (bx * dm.nb + bx) * dm.wpp;
-  static_assert(kTieGroup % 4 == 0, "tie groups hold whole 4-y steps");
+  static_assert(kTieGroupFine % 4 == 0 && kTieGroupCoarse % 4 == 0, "tie groups hold whole 4-y steps");
 
   // the tile stops after a whole merge chunk; folding the last partial
   // early or late does not change H + S
@@ -801,8 +807,8 @@ __device__ __forceinline__ void cohesion_group(const float* __restrict__ Dp, con
   }
   bool tied = true;
   for (int64_t y0 = 0; y0 < n4; y0 += 4) {
-    if (y0 % kTieGroup == 0) {
-      const int64_t g = y0 / kTieGroup;
+    if (y0 % dm.group == 0) {
+      const int64_t g = y0 / dm.group;
       tied = all_long || ((__ldg(trow + (g >> 5)) >> (g & 31)) & 1u);
     }
 #pragma unroll

@@ -52,7 +52,8 @@ static_assert(FG::B == 64 && CG::B == 64 && FG::H == 1 && CG::H == 1, "both pass
 constexpr int kB = 64;
 constexpr int kMaxGridY = 65535;  // matrices beyond it are strided over blockIdx.y
 constexpr int kMaxBatchedN = 4096;
-constexpr int kTieWordsBatched = ((kMaxBatchedN + kTieGroup - 1) / kTieGroup + 31) / 32;
+static_assert(kMaxBatchedN <= kTieFineMaxN, "batched tie maps have fine groups");
+constexpr int kTieWordsBatched = ((kMaxBatchedN + kTieGroupFine - 1) / kTieGroupFine + 31) / 32;
 constexpr int kGroupThreads = 128;  // groups of four points per CTA of the group kernels
 
 // Set by a CTA whose bounded wait gave up (never in normal operation).

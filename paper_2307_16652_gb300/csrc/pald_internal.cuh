@@ -168,35 +168,44 @@ __host__ __device__ __forceinline__ void tri_decode(int64_t t, int64_t T, int* b
 // Pass 2 has a 4-instruction form that is exact unless a one-sided tie
 // d_xy == d_xz (or d_zy == d_zx) occurs; such a tie is two equal entries in
 // one row of D.  The map holds one bit per (pair of 64-blocks {X, Z}, group
-// of 8 consecutive y): set when some row r of X or Z has two equal entries
-// at columns p and q with the block of q being the other side of the pair
-// and p in the y group.  `dirty[b]` marks a block with a row whose repeats
-// were too many to list; every stage of a tile touching it takes the exact
-// loop.  Layout: words[nb][nb][wpp] then dirty[nb], all uint32.  (Groups of
-// 8 y rather than a whole 32-y stage: a sparse tie marks a quarter of the
-// long-form work, and a stage with some marked groups runs the long form
-// on those groups only.)
-constexpr int kTieBlock = 64;  // rows / columns per block of the map
-constexpr int kTieGroup = 8;   // y per group of the map
+// of `group` consecutive y): set when some row r of X or Z has two equal
+// entries at columns p and q with the block of q being the other side of the
+// pair and p in the y group.  `dirty[b]` marks a block with a row whose
+// repeats were too many to list; every stage of a tile touching it takes the
+// exact loop.  Layout: words[nb][nb][wpp] then dirty[nb], all uint32.
+// Groups are 8 y up to n = 65536 (a sparse tie marks a quarter of a 32-y
+// stage, and a stage with some marked groups runs the long form on those
+// groups only), 32 y beyond, where the map's n^3 / 2^18 bytes would grow
+// past 1 GB.
+constexpr int kTieBlock = 64;        // rows / columns per block of the map
+constexpr int kTieGroupFine = 8;     // y per group for n <= kTieFineMaxN
+constexpr int kTieGroupCoarse = 32;  // y per group beyond
+constexpr int64_t kTieFineMaxN = 65536;
 
 struct TieMapDims {
   int64_t nb;   // blocks per side, ceil(n / 64)
-  int64_t wpp;  // words per block pair, ceil(ceil(n / 8) / 32)
+  int64_t wpp;  // words per block pair, ceil(ceil(n / group) / 32)
+  int group;    // y per group
 };
-
-// The bits of one stage of BK y in its word of the map (they never straddle
-// two words): nonzero means some group of the stage needs the long form.
-template <int BK>
-__host__ __device__ constexpr uint32_t tie_stage_mask() {
-  static_assert(BK % kTieGroup == 0 && 32 % (BK / kTieGroup) == 0, "a stage holds whole groups of one word");
-  return BK / kTieGroup == 32 ? ~0u : (1u << (BK / kTieGroup)) - 1u;
-}
 
 __host__ __device__ __forceinline__ TieMapDims tie_map_dims(int64_t n) {
   TieMapDims d;
+  d.group = n <= kTieFineMaxN ? kTieGroupFine : kTieGroupCoarse;
   d.nb = (n + kTieBlock - 1) / kTieBlock;
-  d.wpp = ((n + kTieGroup - 1) / kTieGroup + 31) / 32;
+  d.wpp = ((n + d.group - 1) / d.group + 31) / 32;
   return d;
+}
+
+// The map bits of stage st (BK consecutive y) of one block pair: group g
+// onwards, `mask` wide (low bit first; they never straddle two words).  A
+// nonzero value means some y of the stage need the long form.
+struct TieStage {
+  int64_t g;
+  uint32_t mask;
+};
+__host__ __device__ __forceinline__ TieStage tie_stage(int64_t st, int BK, int group) {
+  const int gps = BK >= group ? BK / group : 1;  // groups per stage (a stage inside one group: 1)
+  return {st * BK / group, gps >= 32 ? ~0u : (1u << gps) - 1u};
 }
 
 // Words of the map including the dirty flags.

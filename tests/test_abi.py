@@ -71,7 +71,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib):
 
 
 def test_tie_map_size():
-    # nb = ceil(n/64) blocks, wpp = ceil(ceil(n/8)/32) words per block pair, plus nb dirty words
+    # nb = ceil(n/64) blocks, wpp = ceil(ceil(n/G)/32) words per block pair, plus nb dirty words;
+    # groups of G = 8 y up to n = 65536, 32 y beyond
     assert binding.pald_tie_map_words(1) == 0
     assert binding.pald_tie_map_words(2) == 1 * 1 * 1 + 1
     assert binding.pald_tie_map_words(64) == 1 + 1
@@ -81,6 +82,8 @@ def test_tie_map_size():
     assert binding.pald_tie_map_words(1024) == 16 * 16 * 4 + 16
     assert binding.pald_tie_map_words(1025) == 17 * 17 * 5 + 17
     assert binding.pald_tie_map_words(65536) == 1024 * 1024 * 256 + 1024
+    assert binding.pald_tie_map_words(65537) == 1025 * 1025 * 65 + 1025
+    assert binding.pald_tie_map_words(147456) == 2304 * 2304 * 144 + 2304
 
 
 def test_batched_argument_checks(lib):
