@@ -255,19 +255,36 @@ __device__ __forceinline__ void cohesion_step2_short(uint64_t& sx, uint64_t& sz,
       : "f"(a1), "f"(a2lo), "f"(a2hi), "f"(S), "f"(clo), "f"(chi), "l"(r1d), "l"(r2p));
 }
 
-// Long form of one pair on lane L of the packed partials (cohesion_step).
-template <int L>
-__device__ __forceinline__ void cohesion_step2_long(uint64_t& sx, uint64_t& sz, float a1, float a2, float S, float c,
-                                                    float r1, float r2) {
-  float x0, x1, z0, z1;
-  unpack2(sx, x0, x1);
-  unpack2(sz, z0, z1);
-  uint64_t p = L == 0 ? pack2(x0, z0) : pack2(x1, z1);
-  cohesion_step(p, a1, a2, S, c, r1, r2);
-  float px, pz;
-  unpack2(p, px, pz);
-  sx = L == 0 ? pack2(px, x1) : pack2(x0, px);
-  sz = L == 0 ? pack2(pz, z1) : pack2(z0, pz);
+// Long form of pairs (i, jj) and (i, jj + 2) on the packed partials: per
+// lane the operations of cohesion_step, with both lanes of sx and sz
+// updated in place.
+__device__ __forceinline__ void cohesion_step2_long(uint64_t& sx, uint64_t& sz, float a1, float a2lo, float a2hi,
+                                                    float S, float clo, float chi, float r1, float r2lo,
+                                                    float r2hi) {
+  asm("{\n\t.reg .pred p0, p1;\n\t"
+      ".reg .f32 m0, m1, t10, t11, t20, t21, v10, v11, v20, v21, x0, x1, z0, z1;\n\t"
+      "mov.b64 {x0, x1}, %0;\n\t"
+      "mov.b64 {z0, z1}, %1;\n\t"
+      "fma.rn.f32 t20, %3, %5, %6;\n\t"
+      "fma.rn.f32 t21, %4, %5, %7;\n\t"
+      "fma.rn.f32 t10, %2, %5, %6;\n\t"
+      "fma.rn.f32 t11, %2, %5, %7;\n\t"
+      "fma.rn.sat.f32 v20, t20, 0f3F000000, 0f3F000000;\n\t"
+      "fma.rn.sat.f32 v21, t21, 0f3F000000, 0f3F000000;\n\t"
+      "fma.rn.sat.f32 v10, t10, 0f3F000000, 0f3F000000;\n\t"
+      "fma.rn.sat.f32 v11, t11, 0f3F000000, 0f3F000000;\n\t"
+      "min.f32 m0, v10, v20;\n\t"
+      "min.f32 m1, v11, v21;\n\t"
+      "setp.gt.f32 p0, m0, 0f00000000;\n\t"
+      "setp.gt.f32 p1, m1, 0f00000000;\n\t"
+      "@p0 fma.rn.f32 x0, v20, %8, x0;\n\t"
+      "@p1 fma.rn.f32 x1, v21, %8, x1;\n\t"
+      "@p0 fma.rn.f32 z0, v10, %9, z0;\n\t"
+      "@p1 fma.rn.f32 z1, v11, %10, z1;\n\t"
+      "mov.b64 %0, {x0, x1};\n\t"
+      "mov.b64 %1, {z0, z1};\n\t}"
+      : "+l"(sx), "+l"(sz)
+      : "f"(a1), "f"(a2lo), "f"(a2hi), "f"(S), "f"(clo), "f"(chi), "f"(r1), "f"(r2lo), "f"(r2hi));
 }
 
 template <class Geo, int MODE, bool SHORT, int U = Geo::UNR>
@@ -305,8 +322,8 @@ __device__ __forceinline__ void cohesion_stage_packed(const float* ad, const flo
           for (int jj = 0; jj < 2; ++jj) {
             float r2lo, r2hi;
             unpack2(r2p[jj], r2lo, r2hi);
-            cohesion_step2_long<0>(sx[i][jj], sz[i][jj], a1[i], a2[jj], S, cv[i][jj], r1, r2lo);
-            cohesion_step2_long<1>(sx[i][jj], sz[i][jj], a1[i], a2[jj + 2], S, cv[i][jj + 2], r1, r2hi);
+            cohesion_step2_long(sx[i][jj], sz[i][jj], a1[i], a2[jj], a2[jj + 2], S, cv[i][jj], cv[i][jj + 2], r1,
+                                r2lo, r2hi);
           }
         }
       }
@@ -348,11 +365,11 @@ template <int BK>
 struct TieCursor {
   const uint32_t* row;
   int64_t nstages;
-  int group;
+  int gshift;
   bool all_long;
   __device__ __forceinline__ TieCursor(const uint32_t* tmap, int64_t n, int64_t X0, int64_t Z0) {
     const TieMapDims dm = tie_map_dims(n);
-    group = dm.group;
+    gshift = dm.gshift;
     const int64_t bx = X0 / kTieBlock, bz = Z0 / kTieBlock;
     row = tmap + (bx * dm.nb + bz) * dm.wpp;
     nstages = (n + BK - 1) / BK;
@@ -362,7 +379,7 @@ struct TieCursor {
   __device__ __forceinline__ uint32_t tied(int64_t st) const {
     if (all_long) return 1u;
     if (st >= nstages) return 0u;
-    const TieStage ts = tie_stage(st, BK, group);
+    const TieStage ts = tie_stage(st, BK, gshift);
     return (__ldg(row + (ts.g >> 5)) >> (ts.g & 31)) & ts.mask;
   }
 };
@@ -622,7 +639,7 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
 
   if (threadIdx.x == 0) ring.init();
   // the tile's tie-map row (all ones when there is no map or a block is dirty)
-  const int group = tie_map_dims(n).group;
+  const int gshift = tie_map_dims(n).gshift;
   {
     const TieMapDims dm = tie_map_dims(n);
     const int64_t bx = bi, bz = bj;  // 64-wide tiles are the map's blocks
@@ -671,7 +688,7 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
       ring, nstages, [&](int q) { ring.issue(q, maps, cols); },
       [&](int st, int buf) {
         if (!active) return;
-        const TieStage ts = tie_stage(st, BK, group);
+        const TieStage ts = tie_stage(st, BK, gshift);
         const uint32_t bits = (tie_words[ts.g >> 5] >> (ts.g & 31)) & ts.mask;
         if (bits == 0u) {
           run(Short(), std::integral_constant<int, Geo::UNR>(), buf, 0, stage_extent<BK, Geo::UNR>(n, st));
@@ -679,7 +696,7 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
           run(Long(), std::integral_constant<int, Geo::UNR>(), buf, 0, stage_extent<BK, Geo::UNR>(n, st));
         } else {  // fine groups only
           const int ke = stage_extent<BK, CH>(n, st);
-          const int gpc = CH / group;  // groups per chunk
+          const int gpc = CH >> gshift;  // groups per chunk
           const uint32_t cmask = (1u << gpc) - 1u;
 #pragma unroll 1
           for (int c = 0; c * CH < ke; ++c) {
@@ -807,8 +824,8 @@ __device__ __forceinline__ void cohesion_group(const float* __restrict__ Dp, con
   }
   bool tied = true;
   for (int64_t y0 = 0; y0 < n4; y0 += 4) {
-    if (y0 % dm.group == 0) {
-      const int64_t g = y0 / dm.group;
+    if ((y0 & (dm.group - 1)) == 0) {
+      const int64_t g = y0 >> dm.gshift;
       tied = all_long || ((__ldg(trow + (g >> 5)) >> (g & 31)) & 1u);
     }
 #pragma unroll

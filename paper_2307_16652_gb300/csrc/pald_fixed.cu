@@ -190,14 +190,14 @@ __global__ void __launch_bounds__(FX::NT, 1)
       Ax[i][j] = 0;
       Az[i][j] = 0;
     }
-  const int group = tie_map_dims(n).group;
+  const int gshift = tie_map_dims(n).gshift;
   const CUtensorMap* const maps[6] = {&tmD, &tmH, &tmL, &tmD, &tmH, &tmL};
   const int cols[6] = {bi * 64, bi * 64, bi * 64, bj * 64, bj * 64, bj * 64};
   const bool ok = tma_pipeline(
       ring, nstages, [&](int q) { ring.issue(q, maps, cols); },
       [&](int st, int buf) {
         if (!active) return;
-        const TieStage ts = tie_stage(st, BK, group);  // any group of the stage marked: long form
+        const TieStage ts = tie_stage(st, BK, gshift);  // any group of the stage marked: long form
         const int kend = stage_extent<BK, 16>(n, st);
         if ((tie_words[ts.g >> 5] >> (ts.g & 31)) & ts.mask)
           fixed_stage<false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2), ring.panel(buf, 3),

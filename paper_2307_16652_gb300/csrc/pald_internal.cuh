@@ -186,11 +186,14 @@ struct TieMapDims {
   int64_t nb;   // blocks per side, ceil(n / 64)
   int64_t wpp;  // words per block pair, ceil(ceil(n / group) / 32)
   int group;    // y per group
+  int gshift;   // log2(group): every group index is a shift, not a 64-bit division
 };
 
 __host__ __device__ __forceinline__ TieMapDims tie_map_dims(int64_t n) {
   TieMapDims d;
+  static_assert(kTieGroupFine == 8 && kTieGroupCoarse == 32, "group sizes are powers of two");
   d.group = n <= kTieFineMaxN ? kTieGroupFine : kTieGroupCoarse;
+  d.gshift = n <= kTieFineMaxN ? 3 : 5;
   d.nb = (n + kTieBlock - 1) / kTieBlock;
   d.wpp = ((n + d.group - 1) / d.group + 31) / 32;
   return d;
@@ -203,9 +206,9 @@ struct TieStage {
   int64_t g;
   uint32_t mask;
 };
-__host__ __device__ __forceinline__ TieStage tie_stage(int64_t st, int BK, int group) {
-  const int gps = BK >= group ? BK / group : 1;  // groups per stage (a stage inside one group: 1)
-  return {st * BK / group, gps >= 32 ? ~0u : (1u << gps) - 1u};
+__host__ __device__ __forceinline__ TieStage tie_stage(int64_t st, int BK, int gshift) {
+  const int gps = BK >= (1 << gshift) ? BK >> gshift : 1;  // groups per stage (a stage inside one group: 1)
+  return {BK >= (1 << gshift) ? st * (BK >> gshift) : (st * BK) >> gshift, gps >= 32 ? ~0u : (1u << gps) - 1u};
 }
 
 // Words of the map including the dirty flags.

@@ -232,14 +232,14 @@ __global__ void __launch_bounds__(PG::NT, 2)
       hacc[i][jj] = pack2(kMergeBias, kMergeBias);
     }
   }
-  const int group = tie_map_dims(n).group;
+  const int gshift = tie_map_dims(n).gshift;
   const CUtensorMap* const maps[3] = {&tmD, &tmR, &tmD};
   const int cols[3] = {bx * 64, static_cast<int>(X0 - x0), bz * 64};
   const bool ok = tma_pipeline(
       ring, nstages, [&](int q) { ring.issue(q, maps, cols); },
       [&](int st, int buf) {
         if (!active) return;
-        const TieStage ts = tie_stage(st, BK, group);  // any group of the stage marked: long form
+        const TieStage ts = tie_stage(st, BK, gshift);  // any group of the stage marked: long form
         const int kend = stage_extent<BK, 16>(n, st);
         if ((tie_words[ts.g >> 5] >> (ts.g & 31)) & ts.mask)
           strip_cohesion_stage<MODE, false>(ring.panel(buf, 0), ring.panel(buf, 1), ring.panel(buf, 2), tx, tz, S,

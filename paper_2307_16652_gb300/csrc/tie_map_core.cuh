@@ -73,7 +73,7 @@ __device__ __forceinline__ void tie_mark(uint32_t* map, const TieMapDims& dm, in
     a = b;
     b = t;
   }
-  const int64_t g = p / dm.group;
+  const int64_t g = p >> dm.gshift;
   atomicOr(map + (a * dm.nb + b) * dm.wpp + (g >> 5), 1u << (g & 31));
 }
 
