@@ -682,6 +682,7 @@ __device__ __forceinline__ bool cohesion_tile_tma(const CUtensorMap* tmD, const 
   // coarse groups cover a stage, so their stages are never mixed)
   constexpr int CH = kTieGroupFine > kMergeEvery ? kTieGroupFine : kMergeEvery;
   static_assert(BK % CH == 0 && CH % kTieGroupFine == 0, "a stage holds whole chunks");
+  static_assert(BK <= kTieGroupCoarse, "a stage lies inside one coarse group (never mixed)");
   const CUtensorMap* const maps[4] = {tmD, tmR, tmD, tmR};
   const int cols[4] = {bi * 64, bi * 64, bj * 64, bj * 64};
   const bool ok = tma_pipeline(
