@@ -157,5 +157,55 @@ def imbalance(n: int, world: int) -> float:
     return max(c) / (sum(c) / len(c)) if sum(c) else 1.0
 
 
+# ---------------------------------------------------------------------------
+# The batched workload over several GPUs: the matrices are independent
+# problems, so each one runs whole on one rank and no rank needs another's
+# data (weak scaling, no collective on the data path).
+
+def batched_partition(ns, world: int):
+    """Matrix indices per rank: largest first (cost n^3, as both passes
+    scale with C(n,3)) to the rank with the least work so far, the lowest
+    rank on ties.  Deterministic; each list ascending."""
+    ns = np.asarray(ns, dtype=np.int64)
+    load = np.zeros(world, dtype=np.float64)
+    parts = [[] for _ in range(world)]
+    for i in sorted(range(len(ns)), key=lambda k: (-int(ns[k]), k)):
+        r = int(np.argmin(load))
+        parts[r].append(i)
+        load[r] += float(ns[i]) ** 3
+    return [np.array(sorted(p), dtype=np.int64) for p in parts]
+
+
+def batched_imbalance(ns, world: int) -> float:
+    """Largest rank's n^3 work over the mean."""
+    ns = np.asarray(ns, dtype=np.float64)
+    cost = [float((ns[p] ** 3).sum()) for p in batched_partition(ns, world)]
+    return max(cost) / (sum(cost) / world) if sum(cost) else 1.0
+
+
+def pald_batched_sharded(ns, offs, D, U, C, *, rank: int = None, world: int = None, group=None,
+                         accum_mode: int = 0, stream=None):
+    """This rank's share of a batched workload: ``pald_batched`` on the
+    matrices ``batched_partition`` gives it, in the caller's packed buffers
+    (every rank may hold all of D; only its own matrices' U and C are
+    written).  `rank` and `world` default to the process group's.  Returns
+    the rank's matrix indices."""
+    import torch.distributed as dist
+
+    from . import binding
+
+    if world is None:
+        world = dist.get_world_size(group) if dist.is_initialized() else 1
+    if rank is None:
+        rank = dist.get_rank(group) if dist.is_initialized() else 0
+    ns = np.asarray(ns, dtype=np.int64)
+    offs = np.asarray(offs, dtype=np.int64)
+    mine = batched_partition(ns, world)[rank]
+    if len(mine):
+        binding.pald_batched(ns[mine], offs[mine], D, U, C, accum_mode=accum_mode, stream=stream)
+    return mine
+
+
 __all__ = ["B", "TILE_WORDS", "tiles_of", "shard_range", "tile_order", "pack_tiles", "unpack_tiles", "max_range",
-           "pald_sharded", "tiles_per_rank_cost", "imbalance"]
+           "pald_sharded", "tiles_per_rank_cost", "imbalance", "batched_partition", "batched_imbalance",
+           "pald_batched_sharded"]

@@ -148,3 +148,64 @@ def test_library_shard_ranges_match_the_host_plan():
     assert binding.pald_shard_tiles(1) == 0
     with pytest.raises(binding.PaldError):
         binding.pald_shard_range(100, 2, 2)
+
+
+# ---------------------------------------------------------------------------
+# The batched workload over ranks: whole matrices per rank, no exchange.
+
+@pytest.mark.parametrize("world", [1, 2, 3, 8])
+def test_batched_partition_covers_every_matrix_once(world):
+    ns = inputs.batched_sizes(2000)
+    parts = shard.batched_partition(ns, world)
+    assert len(parts) == world
+    assert sorted(np.concatenate(parts).tolist()) == list(range(len(ns)))
+    assert all(np.all(np.diff(p) > 0) for p in parts)  # ascending, no repeats
+    assert shard.batched_imbalance(ns, world) < 1.01   # 2000 matrices balance closely by n^3
+
+
+def test_batched_partition_with_more_ranks_than_matrices():
+    parts = shard.batched_partition([5, 300, 9], 5)
+    assert sorted(np.concatenate(parts).tolist()) == [0, 1, 2]
+    assert sum(len(p) == 0 for p in parts) == 2
+    assert parts[0].tolist() == [1]  # the largest goes first, to rank 0
+
+
+def _batched_worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ns = inputs.batched_sizes(12, lo=8, hi=70)
+        mine = shard.batched_partition(ns, world)[rank]
+        out = {}
+        for i in mine:  # this rank's matrices only; nothing from the other rank is needed
+            U, C = oracle.focus_and_cohesion(inputs.euclidean_fp32(inputs.batched_points(int(i), int(ns[i]))),
+                                             threads=1)
+            out[int(i)] = (U, C)
+        everyone = [None] * world
+        dist.all_gather_object(everyone, out)  # for the check only
+        if rank == 0:
+            merged = {}
+            for part in everyone:
+                assert not set(part) & set(merged), "a matrix ran on two ranks"
+                merged.update(part)
+            ok = sorted(merged) == list(range(len(ns)))
+            for i, (U, C) in merged.items():
+                Ur, Cr = oracle.focus_and_cohesion(inputs.euclidean_fp32(inputs.batched_points(i, int(ns[i]))),
+                                                   threads=1)
+                ok = ok and np.array_equal(U, Ur) and np.array_equal(C, Cr)
+            q.put(ok)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_ranks_run_disjoint_batched_shares():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_batched_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    assert q.get(timeout=10)

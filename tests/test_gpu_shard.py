@@ -103,3 +103,30 @@ def test_bad_ranges_are_rejected():
     with pytest.raises(binding.PaldError):
         binding.pald_focus_tiles(D, U, 5, 4)
     assert lib.pald_pack_tiles(U.data_ptr(), n, 0, 1, 2, U.data_ptr(), None) == 1  # both must be 0 or 1
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_batched_shares_run_one_after_another_give_the_full_result(world):
+    # each rank's pald_batched over its own matrices, into shared packed
+    # buffers: together they must equal one pald_batched call bit for bit
+    rng = np.random.default_rng(world)
+    ns = np.array([int(v) for v in rng.integers(8, 300, size=40)] + [513, 1024], dtype=np.int64)
+    offs, total = inputs.packed_offsets(ns)
+    Dh = np.zeros(total, np.float32)
+    for i, n in enumerate(ns):
+        Dh[offs[i]:offs[i] + n * n] = inputs.euclidean_fp32(inputs.batched_points(i, int(n))).ravel()
+    D = torch.from_numpy(Dh).cuda()
+    U1 = torch.zeros(total, dtype=torch.int32, device="cuda")
+    C1 = torch.zeros(total, dtype=torch.float32, device="cuda")
+    binding.pald_batched(ns, offs, D, U1, C1)
+    U2 = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+    C2 = torch.full((total,), -1.0, dtype=torch.float32, device="cuda")
+    seen = []
+    for r in range(world):
+        seen += shard.pald_batched_sharded(ns, offs, D, U2, C2, rank=r, world=world).tolist()
+    torch.cuda.synchronize()
+    assert sorted(seen) == list(range(len(ns)))
+    assert binding.pald_check_faults() == 0
+    for i, n in enumerate(ns):
+        sl = slice(int(offs[i]), int(offs[i] + n * n))
+        assert torch.equal(U2[sl], U1[sl]) and torch.equal(C2[sl], C1[sl]), f"matrix {i} (n = {n})"
