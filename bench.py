@@ -385,8 +385,8 @@ def run_other_workloads(props, sm_max):
     """Per-pass rates on the other single-matrix configs: tie-heavy-4096 (a
     tie in nearly every 8-y group: pass 2 runs its 8-slot long form
     throughout) and precision-16384; on the paper recipe at n = 8192, pass 2
-    with the fused local depth and the pairwise strip variant (u never
-    stored)."""
+    with the fused local depth, pass 2 in each accumulation mode and the
+    pairwise strip variant (u never stored)."""
     import torch
 
     import paper_2307_16652_gb300 as pald
@@ -444,6 +444,13 @@ def run_other_workloads(props, sm_max):
                                "local_depth_pass_ms": round(ms_sep, 3),
                                "note": "pass 2 with the row sums in its epilogue vs pass 2 alone and the "
                                        "separate O(n^2) pass over C"}
+    modes = {"compensated": ms_c}
+    for name, mode in (("plain_fp32", pald.PALD_ACCUM_PLAIN), ("fixed_point", pald.PALD_ACCUM_FIXED)):
+        modes[name] = timed(lambda: pald.pald_cohesion(D, U, C, accum_mode=mode), 2)
+    out["accum-modes-paper-8192"] = {
+        "n": n, **{f"{k}_ms": round(v, 3) for k, v in modes.items()},
+        **{f"{k}_frac_of_issue_peak": OPS_PER_TRIPLET["cohesion"] * triplets(n) / (v / 1e3) / peak_ops
+           for k, v in modes.items()}}
     del U, L
     ms = timed(lambda: pald.pald_pairwise(D, C), 2)
     out["pairwise-paper-8192"] = {"n": n, "ms_both_passes": round(ms, 3),
