@@ -68,6 +68,27 @@ def test_paper_65536_sampled_rows_and_invariants():
     assert abs(float(total) - n / 2) < 1e-6 * n
 
 
+def test_past_the_fine_tie_map_order_sampled_rows():
+    # beyond n = 65536 the tie map has groups of 32 y (one per stage); n % 64
+    # == 4 leaves a ragged last tile row and column
+    n = 65540
+    nb = -(-n // 64)
+    assert binding.pald_tie_map_words(n) == nb * nb * (-(-(-(-n // 32)) // 32)) + nb
+    D = inputs.euclidean_fp32_torch(inputs.paper_points(n), "cuda")
+    U = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    C = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    binding.pald_focus(D, U)
+    binding.pald_cohesion(D, U, C)
+    torch.cuda.synchronize()
+    assert binding.pald_check_faults() == 0
+    rng = np.random.default_rng(n)
+    rows = np.unique(np.concatenate([[0, 65536, n - 1], rng.choice(n, size=5, replace=False)]))
+    Ur, Cr = oracle.rows(D.cpu().numpy(), rows)
+    idx = torch.from_numpy(rows).cuda()
+    mx, mean = check_rows(U[idx].cpu().numpy(), C[idx].cpu().numpy(), Ur, Cr)
+    print(f"n={n} (coarse tie map) sampled {len(rows)} rows: max rel {mx:.3e} mean {mean:.3e}")
+
+
 def _batched_inputs(count):
     ns = inputs.batched_sizes(count)
     offs, total = inputs.packed_offsets(ns)
