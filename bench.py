@@ -373,7 +373,9 @@ def run_ours(args, rank, world, local):
         v, dt, cores = oracle_rows_rate(Dh, n, k, seed=1)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "sample": f"{k} random rows of the same n={n} matrix, both passes "
-                                         f"({dt:.1f} s), scaled by n/{k}"}
+                                         f"({dt:.1f} s), scaled by n/{k}",
+                               # the whole matrix at the sampled rate (the oracle's work grows as n^3)
+                               "full_extrapolated_s": round(2.0 * triplets(n) / v, 1)}
     if rank == 0 and not args.no_batched:
         out["batched"] = run_batched_compare(args)
     if rank == 0 and not args.no_extras:
